@@ -1,0 +1,172 @@
+/*
+ * fth.h -- C ABI of the GB300 f-thermostat (FTH) library (libfth.so).
+ *
+ * The f-thermostat (Nava, Ceriotti, Dryzun, Parrinello, "Evaluating functions of
+ * positive-definite matrices using colored noise thermostats") estimates elements of
+ * f(M) for a symmetric positive-definite M.  M is the Hessian of the harmonic
+ * potential V(q) = q^T M q / 2 (Eq. 5); every Cartesian degree of freedom carries the
+ * same Markovian generalized-Langevin thermostat (Eq. 2) with drift A_p and
+ * free-particle covariance C_p (Eq. 4), fitted so that a normal mode of frequency w
+ * has momentum fluctuations <p^2>(w) = f(w^2).  Then <p_i p_j> = f(M)_ij (Eq. 6), and
+ * averaging over time and over R independent replicas gives the estimate.
+ *
+ * Integrator: the modified velocity Verlet scheme the paper cites; per step
+ *   O(dt/2) B(dt/2) A(dt) [F = -M q] B(dt/2) O(dt/2)
+ * with O: (p, s) <- T (p, s) + S xi,  T = exp(-A_p dt/2),  S S^T = C_p - T C_p T^T,
+ * S lower triangular (a pivot at or below 1e-14 of the largest diagonal entry is an
+ * exact zero), xi standard normals from Philox4x32-10 (counter (kappa, i, r, k), key
+ * = seed) through Box-Muller.  Samples of p (or q) are taken at the end of each step.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an fth_status; none aborts.  After an error,
+ *    fth_last_error(ctx) describes it (ctx may be NULL for create-time errors, then
+ *    the message is thread-local).
+ *  - Host buffers belong to the caller and are only read during the call.
+ *  - Device memory: the library allocates none.  The caller provides one device
+ *    workspace of fth_workspace_size() bytes (e.g. a torch uint8 tensor) that must
+ *    outlive the context; all state, copies of M, samples and accumulators live there.
+ *  - Work is enqueued on opt.stream (a cudaStream_t, NULL = legacy default stream);
+ *    fth_run returns once enqueued.  Calls that return data synchronise that stream.
+ *  - Results are FP64.  (i, j) and (j, i) name the same element.
+ *  - A context is not thread-safe: use one per host thread.
+ *  - State planes exchanged with the host use the replica-major layout [R][N]
+ *    (s: [R][s][N]) in FP64.
+ */
+#ifndef FTH_H
+#define FTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fth_ctx fth_ctx;
+
+typedef enum {
+    FTH_OK = 0,
+    FTH_E_INVALID_ARG = 1,   /* bad size, pointer, enum value or GLE               */
+    FTH_E_NOT_SPD = 2,       /* M fails the positive-definiteness precondition     */
+    FTH_E_UNSUPPORTED = 3,   /* valid request with no kernel here (e.g. s > 4)     */
+    FTH_E_WORKSPACE = 4,     /* workspace NULL, misaligned or too small            */
+    FTH_E_CUDA = 5,          /* a CUDA runtime call failed                         */
+    FTH_E_TIMEOUT = 6,       /* a device wait gave up (bounded spin)               */
+    FTH_E_NONFINITE = 7,     /* NaN/Inf found in the accumulators at a block flush */
+    FTH_E_NOT_TRACKED = 8    /* fth_elements asked for an unregistered element     */
+} fth_status;
+
+enum fth_matrix_kind { FTH_DENSE = 0, FTH_CSR = 1 };
+enum fth_dtype { FTH_F32 = 0, FTH_F64 = 1 };
+
+/* Arithmetic of the force F = -M Q (all forms accumulate in FP32 except FP64):
+ *   FP32    plain FP32 FFMA GEMM / SpMM;
+ *   TF32    tcgen05 kind::tf32 tensor-core GEMM (dense only);
+ *   BF16X3  tcgen05 kind::f16 with split BF16 operands, hi*hi + hi*lo + lo*hi (dense only);
+ *   FP64    FP64 state and arithmetic, one CTA per replica (dense, N <= 1024).     */
+enum fth_precision { FTH_PREC_FP32 = 0, FTH_PREC_TF32 = 1, FTH_PREC_BF16X3 = 2, FTH_PREC_FP64 = 3 };
+
+/* Which elements of <x x^T> are accumulated (sized at create, paper's "2A" reals):
+ *   LIST  the opt.pairs list;  DIAG  all (i, i);  ALL  every element (dense only).  */
+enum fth_track { FTH_TRACK_LIST = 0, FTH_TRACK_DIAG = 1, FTH_TRACK_ALL = 2 };
+
+/* Sampled variable: p (Eq. 6, default) or q. */
+enum fth_observable { FTH_OBS_P = 0, FTH_OBS_Q = 1 };
+
+enum fth_plane { FTH_PLANE_Q = 0, FTH_PLANE_P = 1, FTH_PLANE_S = 2 };
+
+typedef struct {
+    int kind;               /* FTH_DENSE or FTH_CSR                                       */
+    int dtype;              /* FTH_F32 or FTH_F64: element type of `values`               */
+    int on_device;          /* 0: host pointers; 1: device pointers                       */
+    int64_t n;              /* order N >= 1                                               */
+    int64_t nnz;            /* CSR: number of stored entries                              */
+    const void* values;     /* dense: N*N row-major; CSR: nnz values                      */
+    const int32_t* rowptr;  /* CSR: N+1 offsets, rowptr[0] = 0, non-decreasing            */
+    const int32_t* colind;  /* CSR: nnz column indices in [0, N)                          */
+} fth_matrix;
+
+typedef struct {
+    int s;                  /* auxiliary momenta per dof, 0 <= s <= 4                      */
+    double a_p[25];         /* drift A_p, (s+1)x(s+1) row-major in the leading entries     */
+    double c_p[25];         /* free-particle covariance C_p, (s+1)x(s+1) row-major         */
+} fth_gle;
+
+typedef struct {
+    int64_t replicas;       /* R >= 1 independent replicas                                 */
+    uint64_t seed;          /* Philox key                                                  */
+    double dt;              /* time step > 0                                               */
+    int64_t burnin;         /* samples discarded before accumulation starts                */
+    int64_t block;          /* samples per block for the error bars (>= 1)                */
+    int observable;         /* enum fth_observable                                        */
+    int precision;          /* enum fth_precision                                         */
+    int track;              /* enum fth_track                                             */
+    const int64_t* pairs;   /* LIST: host array of 2*npairs indices (i, j)                */
+    int64_t npairs;
+    int64_t stack;          /* samples staged before one accumulation pass (0 = auto)     */
+    void* stream;           /* cudaStream_t                                               */
+} fth_options;
+
+typedef struct {
+    int64_t steps;          /* completed steps                                             */
+    int64_t samples;        /* samples taken (burn-in included)                            */
+    int64_t accumulated;    /* samples accumulated                                         */
+    int64_t blocks;         /* completed blocks                                            */
+    int64_t launches;       /* kernels launched by this context so far                     */
+    int primed;             /* 1 if the start half of the next step is already applied     */
+    int precision;          /* precision actually used                                     */
+    int64_t n, replicas, tracked;
+    size_t workspace_bytes;
+} fth_info_t;
+
+/* Bytes of device workspace fth_create needs for this problem (no device access). */
+fth_status fth_workspace_size(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
+                              size_t* bytes);
+
+/* Validate the problem, build T and S in FP64 on the host, copy M into the workspace
+ * (converted/rounded for the chosen precision) and zero the state: q = p = s = 0 at a
+ * step boundary.  `workspace` must be 256-byte aligned device memory of at least
+ * fth_workspace_size() bytes.  Enqueues its copies on opt->stream.
+ * Errors: INVALID_ARG, NOT_SPD (a diagonal entry <= 0), UNSUPPORTED, WORKSPACE, CUDA. */
+fth_status fth_create(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
+                      void* workspace, size_t workspace_bytes, fth_ctx** out);
+
+/* Advance the dynamics by `steps` steps, taking one sample per step (the hot path:
+ * force, B, O, sample, O, B, A per step, plus one accumulation pass per `stack`
+ * samples and one FP64 block flush per completed block).  Asynchronous. */
+fth_status fth_run(fth_ctx* ctx, int64_t steps);
+
+/* Estimates of <x_i x_j> for k pairs (2k indices): values[e] = mean over every
+ * accumulated sample and replica; errbars[e] = standard error of the mean of the
+ * completed block means (NaN with fewer than 2 blocks).  Synchronises the stream.
+ * Errors: NOT_TRACKED if a pair is not accumulated, NONFINITE, CUDA. */
+fth_status fth_elements(fth_ctx* ctx, const int64_t* pairs, int64_t k, double* values,
+                        double* errbars);
+
+/* Copy one state plane to / from the host in FP64, layout [R][N] ([R][s][N] for s). */
+fth_status fth_get_state(fth_ctx* ctx, int plane, double* host);
+fth_status fth_set_state(fth_ctx* ctx, int plane, const double* host);
+
+/* Counters and configuration of a context. */
+fth_status fth_info(const fth_ctx* ctx, fth_info_t* info);
+
+/* Synchronise and report the device error word (TIMEOUT, NONFINITE) or FTH_OK. */
+fth_status fth_status_poll(fth_ctx* ctx);
+
+/* Last error message of ctx (or of this thread when ctx is NULL). */
+const char* fth_last_error(const fth_ctx* ctx);
+
+/* Release host resources; the caller then frees the workspace. */
+void fth_destroy(fth_ctx* ctx);
+
+/* The library's own O half-step constants in FP64: T = exp(-A_p dt/2) (Pade scaling
+ * and squaring) and lower-triangular S with S S^T = C_p - T C_p T^T; (s+1)^2 each. */
+fth_status fth_gle_propagator(const fth_gle* gle, double dt, double* T, double* S);
+
+/* Library version string. */
+const char* fth_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTH_H */

@@ -124,3 +124,35 @@ def force(M, q):
     native.lib().oracle_force(native.I64(n), native.I64(R), native.INT(0), native.ptr(M), None,
                               None, None, native.ptr(q), native.ptr(F))
     return F
+
+
+def fused_step_elements(M, q, p, s, T, S, dt, seed, kappa, elems, observable=0):
+    """One fused launch (kick index kappa) for a few sampled (i, r), computed one by
+    one: force (M q_r)_i from the full current positions, then B(dt/2), O(dt/2),
+    sample, O(dt/2), B(dt/2), A(dt) on that (i, r) alone.
+
+    M: [N][N] float64 array or scipy.sparse CSR matrix, q/p: [R][N], s: [R][ns-1][N];
+    elems: iterable of (i, r).
+    Returns arrays (q_new, p_new, s_new[ns-1], sample) per element."""
+    ns = T.shape[0]
+    out_q, out_p, out_s, out_x = [], [], [], []
+    for i, r in elems:
+        i, r = int(i), int(r)
+        if hasattr(M, "getrow"):          # scipy.sparse matrix
+            mq = float((M.getrow(i) @ q[r])[0])
+        else:
+            mq = float(np.dot(M[i], q[r]))
+        xi = native.normals(seed, kappa, i, r, 2 * ns)
+        v = np.concatenate([[p[r, i]], s[r, :, i]])
+        qi = float(q[r, i])
+        v[0] -= 0.5 * dt * mq
+        v = T @ v + S @ xi[:ns]
+        x = qi if observable else v[0]
+        v = T @ v + S @ xi[ns:]
+        v[0] -= 0.5 * dt * mq
+        qi += dt * v[0]
+        out_q.append(qi)
+        out_p.append(v[0])
+        out_s.append(v[1:].copy())
+        out_x.append(x)
+    return np.array(out_q), np.array(out_p), np.array(out_s), np.array(out_x)

@@ -115,7 +115,26 @@ def mode_response(lams, T, S, dt, observable: int = 0) -> np.ndarray:
 
 def mode_response_mean(lams, T, S, dt, burnin: int, nsamples: int, observable: int = 0):
     """Exact expected running mean of x^2 over samples burnin..burnin+nsamples-1 from
-    the zero initial state, per mode."""
+    the zero initial state, per mode.
+
+    From C_k - C = G (C_{k-1} - C) G^T and C_{-1} = 0: C_k = C - G^{k+1} C G^{k+1 T}, so
+    the mean over k = b..b+n-1 is C - (1/n) [G^{b+1} X G^{b+1 T} - G^{b+n+1} X G^{b+n+1 T}]
+    with X = sum_j G^j C G^{j T}, the solution of X = G X G^T + C."""
+    idx = IP if observable == 0 else IQ
+    out = []
+    for l in np.ravel(lams):
+        G, Qn = mode_chain(float(l), T, S, dt)
+        C = sla.solve_discrete_lyapunov(G, Qn)
+        X = sla.solve_discrete_lyapunov(G, C)
+        Ga = np.linalg.matrix_power(G, burnin + 1)
+        Gb = np.linalg.matrix_power(G, burnin + nsamples + 1)
+        tail = (Ga @ X @ Ga.T - Gb @ X @ Gb.T) / nsamples
+        out.append(float(C[idx, idx] - tail[idx, idx]))
+    return np.asarray(out)
+
+
+def mode_response_mean_recursive(lams, T, S, dt, burnin: int, nsamples: int, observable=0):
+    """Same quantity by running the covariance recursion sample by sample."""
     idx = IP if observable == 0 else IQ
     out = []
     for l in np.ravel(lams):

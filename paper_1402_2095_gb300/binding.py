@@ -1,0 +1,260 @@
+"""Thin Python binding of libfth.so (the C ABI declared in include/fth.h).
+
+Argument marshalling only: every step of the f-thermostat path runs in the
+library's CUDA kernels.  PyTorch supplies the device workspace (one uint8 tensor)
+and the CUDA stream.  There is no CPU fallback: if libfth.so is missing the import
+of this module's FTH class fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfth.so")
+
+FTH_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "UNSUPPORTED", 4: "WORKSPACE", 5: "CUDA",
+          6: "TIMEOUT", 7: "NONFINITE", 8: "NOT_TRACKED"}
+DENSE, CSR = 0, 1
+F32, F64 = 0, 1
+PRECISION = {"fp32": 0, "tf32": 1, "bf16x3": 2, "fp64": 3}
+TRACK = {"list": 0, "diag": 1, "all": 2}
+OBSERVABLE = {"p": 0, "q": 1}
+PLANE = {"q": 0, "p": 1, "s": 2}
+
+# Every symbol include/fth.h declares.
+EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_get_state",
+           "fth_set_state", "fth_info", "fth_status_poll", "fth_last_error", "fth_destroy",
+           "fth_gle_propagator", "fth_version")
+
+
+class FthError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fth: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fth_matrix(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("on_device", ctypes.c_int),
+                ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("values", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p)]
+
+
+class fth_gle(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("a_p", ctypes.c_double * 25), ("c_p", ctypes.c_double * 25)]
+
+
+class fth_options(ctypes.Structure):
+    _fields_ = [("replicas", ctypes.c_int64), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("burnin", ctypes.c_int64), ("block", ctypes.c_int64), ("observable", ctypes.c_int),
+                ("precision", ctypes.c_int), ("track", ctypes.c_int), ("pairs", ctypes.c_void_p),
+                ("npairs", ctypes.c_int64), ("stack", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class fth_info_t(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("accumulated", ctypes.c_int64), ("blocks", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("primed", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n", ctypes.c_int64), ("replicas", ctypes.c_int64), ("tracked", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfth.so and declare its signatures; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FthError(5, f"{path} not found: build it with paper_1402_2095_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    P, I64, INT, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "fth_workspace_size": ([P, P, P, P], INT),
+        "fth_create": ([P, P, P, P, ctypes.c_size_t, P], INT),
+        "fth_run": ([P, I64], INT),
+        "fth_elements": ([P, P, I64, P, P], INT),
+        "fth_get_state": ([P, INT, P], INT),
+        "fth_set_state": ([P, INT, P], INT),
+        "fth_info": ([P, P], INT),
+        "fth_status_poll": ([P], INT),
+        "fth_last_error": ([P], ctypes.c_char_p),
+        "fth_destroy": ([P], None),
+        "fth_gle_propagator": ([P, D, P, P], INT),
+        "fth_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != FTH_OK:
+        msg = load().fth_last_error(ctx)
+        raise FthError(status, msg.decode() if msg else "")
+
+
+def make_gle(a_p, c_p) -> fth_gle:
+    a_p = np.asarray(a_p, dtype=np.float64)
+    c_p = np.asarray(c_p, dtype=np.float64)
+    ns = a_p.shape[0]
+    g = fth_gle()
+    g.s = ns - 1
+    for k, x in enumerate(a_p.ravel()):
+        g.a_p[k] = x
+    for k, x in enumerate(c_p.ravel()):
+        g.c_p[k] = x
+    return g
+
+
+def gle_propagator(a_p, c_p, dt):
+    """The library's own FP64 (T, S) of the O half-step."""
+    g = make_gle(a_p, c_p)
+    ns = g.s + 1
+    T = np.zeros(ns * ns)
+    S = np.zeros(ns * ns)
+    _check(load().fth_gle_propagator(ctypes.byref(g), dt, T.ctypes.data, S.ctypes.data))
+    return T.reshape(ns, ns), S.reshape(ns, ns)
+
+
+class FTH:
+    """One f-thermostat problem instance on the current CUDA device.
+
+    M: dense (N x N numpy array or torch tensor, host or device) or csr=(rowptr, col,
+    val, n).  a_p, c_p: the fitted GLE.  The workspace is a torch uint8 tensor held by
+    this object; work runs on `stream` (default: torch's current stream)."""
+
+    def __init__(self, M=None, csr=None, *, a_p, c_p, dt, replicas, seed=0, burnin=0,
+                 block=1000, observable="p", precision="fp32", track="list", pairs=None,
+                 stack=0, stream=None):
+        import torch
+
+        L = load()
+        self._keep = []
+        mat = fth_matrix()
+        if (M is None) == (csr is None):
+            raise ValueError("give exactly one of M or csr")
+        if M is not None:
+            mat.kind = DENSE
+            if isinstance(M, torch.Tensor):
+                t = M.contiguous()
+                mat.dtype = F64 if t.dtype == torch.float64 else F32
+                if t.dtype not in (torch.float32, torch.float64):
+                    t = t.float()
+                mat.on_device = 1 if t.is_cuda else 0
+                mat.values = t.data_ptr()
+                mat.n = t.shape[0]
+                self._keep.append(t)
+            else:
+                a = np.ascontiguousarray(M)
+                if a.dtype not in (np.float32, np.float64):
+                    a = a.astype(np.float64)
+                mat.dtype = F64 if a.dtype == np.float64 else F32
+                mat.on_device = 0
+                mat.values = a.ctypes.data
+                mat.n = a.shape[0]
+                self._keep.append(a)
+        else:
+            rowptr, col, val, n = csr
+            rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(col, dtype=np.int32)
+            va = np.ascontiguousarray(val)
+            if va.dtype not in (np.float32, np.float64):
+                va = va.astype(np.float64)
+            mat.kind = CSR
+            mat.dtype = F64 if va.dtype == np.float64 else F32
+            mat.on_device = 0
+            mat.n = int(n)
+            mat.nnz = int(ci.size)
+            mat.values = va.ctypes.data
+            mat.rowptr = rp.ctypes.data
+            mat.colind = ci.ctypes.data
+            self._keep += [rp, ci, va]
+        self.n = int(mat.n)
+        self.replicas = int(replicas)
+        gle = make_gle(a_p, c_p)
+        self.s = gle.s
+        opt = fth_options()
+        opt.replicas = int(replicas)
+        opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        opt.dt = float(dt)
+        opt.burnin = int(burnin)
+        opt.block = int(block)
+        opt.observable = OBSERVABLE[observable]
+        opt.precision = PRECISION[precision]
+        opt.track = TRACK[track]
+        if pairs is not None:
+            pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+            self._keep.append(pr)
+            opt.pairs = pr.ctypes.data
+            opt.npairs = pr.shape[0]
+        opt.stack = int(stack)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opt.stream = self.stream.cuda_stream
+        nbytes = ctypes.c_size_t(0)
+        _check(L.fth_workspace_size(ctypes.byref(mat), ctypes.byref(gle), ctypes.byref(opt),
+                                    ctypes.byref(nbytes)))
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8,
+                                         device="cuda")
+        ctx = ctypes.c_void_p()
+        _check(L.fth_create(ctypes.byref(mat), ctypes.byref(gle), ctypes.byref(opt),
+                            self.workspace.data_ptr(), self.workspace.numel(), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self._keep_inputs = self._keep  # host copies are only read during create
+        self._keep = []
+
+    # -------------------------------------------------------------- hot path
+    def run(self, steps: int):
+        _check(load().fth_run(self.ctx, int(steps)), self.ctx)
+
+    def elements(self, pairs):
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        k = pr.shape[0]
+        vals = np.zeros(k)
+        errs = np.zeros(k)
+        _check(load().fth_elements(self.ctx, pr.ctypes.data, k, vals.ctypes.data, errs.ctypes.data),
+               self.ctx)
+        return vals, errs
+
+    # -------------------------------------------------------------- state
+    def get_state(self, plane: str):
+        shape = (self.replicas, self.s, self.n) if plane == "s" else (self.replicas, self.n)
+        out = np.zeros(shape)
+        if out.size:
+            _check(load().fth_get_state(self.ctx, PLANE[plane], out.ctypes.data), self.ctx)
+        return out
+
+    def set_state(self, plane: str, arr):
+        shape = (self.replicas, self.s, self.n) if plane == "s" else (self.replicas, self.n)
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(shape))
+        if a.size:
+            _check(load().fth_set_state(self.ctx, PLANE[plane], a.ctypes.data), self.ctx)
+
+    def info(self) -> dict:
+        i = fth_info_t()
+        _check(load().fth_info(self.ctx, ctypes.byref(i)), self.ctx)
+        return {f: getattr(i, f) for f, _ in fth_info_t._fields_}
+
+    def poll(self):
+        _check(load().fth_status_poll(self.ctx), self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().fth_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1037 @@
+// Host runtime of libfth.so: the C ABI of include/fth.h.
+//
+// fth_create validates the problem, builds the O half-step constants in FP64
+// (T = exp(-A_p dt/2), S S^T = C_p - T C_p T^T, Eq. 4 and the cited GLE velocity
+// Verlet scheme), carves the caller's device workspace and uploads M.  fth_run
+// enqueues, per step, the force (Eq. 5) and the fused GLE step (Eq. 2) on the
+// caller's stream, staging one sample per step, and per `stack` samples one
+// accumulation pass of the tracked <x_i x_j> (Eq. 6), per `block` samples one FP64
+// block flush (the paper's block averaging of the 2A accumulators).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "fth.h"
+#include "fth_internal.h"
+
+using namespace fth;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+constexpr int64_t kGatherChunk = 65536;
+
+int64_t round_up(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+enum Path { kPathDense32 = 0, kPathCsr = 1, kPathDense64 = 2 };
+
+// Problem geometry and workspace offsets, computed identically by
+// fth_workspace_size and fth_create.
+struct Layout {
+    Path path;
+    int ns;
+    int precision, track;
+    int64_t N, R, Rp, Np, nnz, stack, ps_ld, ntracked, count, nbt;
+    size_t off_M = 0, off_Mlo = 0, off_rowptr = 0, off_col = 0, off_val = 0;
+    size_t off_q0 = 0, off_q1 = 0, off_p = 0, off_s = 0, off_MQ = 0, off_ophi = 0, off_oplo = 0;
+    size_t off_ps = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
+    size_t off_gidx = 0, off_gout = 0, off_err = 0;
+    size_t total = 0;
+};
+
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off = align256(off + std::max<size_t>(bytes, 1));
+        return o;
+    }
+};
+
+fth_status fail(std::string* where, fth_status st, const std::string& msg) {
+    if (where) *where = msg;
+    else g_thread_error = msg;
+    return st;
+}
+
+// ------------------------------------------------------------------ FP64 propagator
+// exp(X) by scaling and squaring with a degree-20 Taylor polynomial: X is scaled by
+// 2^-j until its 1-norm is at most 1/2, where the truncated series error is below
+// 0.5^21 / 21! (far under FP64 round-off), then squared j times.
+void mat_mul(int n, const double* a, const double* b, double* c) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += a[i * n + k] * b[k * n + j];
+            c[i * n + j] = acc;
+        }
+}
+
+void mat_exp(int n, const double* x, double* out) {
+    double norm = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double col = 0.0;
+        for (int i = 0; i < n; ++i) col += std::fabs(x[i * n + j]);
+        norm = std::max(norm, col);
+    }
+    int sq = 0;
+    double scale = 1.0;
+    while (norm * scale > 0.5) {
+        scale *= 0.5;
+        ++sq;
+    }
+    std::vector<double> xs(n * n), term(n * n), tmp(n * n);
+    for (int k = 0; k < n * n; ++k) xs[k] = x[k] * scale;
+    for (int k = 0; k < n * n; ++k) out[k] = (k % (n + 1) == 0) ? 1.0 : 0.0;
+    for (int k = 0; k < n * n; ++k) term[k] = out[k];
+    for (int d = 1; d <= 20; ++d) {
+        mat_mul(n, term.data(), xs.data(), tmp.data());
+        for (int k = 0; k < n * n; ++k) {
+            term[k] = tmp[k] / d;
+            out[k] += term[k];
+        }
+    }
+    for (int s = 0; s < sq; ++s) {
+        mat_mul(n, out, out, tmp.data());
+        std::copy(tmp.begin(), tmp.end(), out);
+    }
+}
+
+// Lower-triangular L with L L^T = a (symmetric PSD); a pivot at or below
+// 1e-14 * max diag is an exact zero and its column is left zero.
+void chol_psd(int n, const double* a_in, double* L) {
+    std::vector<double> a(a_in, a_in + n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) a[i * n + j] = a[j * n + i] = 0.5 * (a[i * n + j] + a[j * n + i]);
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) dmax = std::max(dmax, a[i * n + i]);
+    const double tol = 1e-14 * dmax;
+    std::fill(L, L + n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = a[j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > tol)) continue;
+        const double ljj = std::sqrt(d);
+        L[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = a[i * n + j];
+            for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = v / ljj;
+        }
+    }
+}
+
+fth_status propagator(const fth_gle* gle, double dt, double* T, double* S, std::string* msg) {
+    if (!gle) return fail(msg, FTH_E_INVALID_ARG, "gle is NULL");
+    const int ns = gle->s + 1;
+    if (gle->s < 0 || ns > kMaxNs) return fail(msg, FTH_E_UNSUPPORTED, "s must be in [0, 4]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(msg, FTH_E_INVALID_ARG, "dt must be > 0");
+    std::vector<double> x(ns * ns), tct(ns * ns), tmp(ns * ns), tt(ns * ns);
+    for (int k = 0; k < ns * ns; ++k) {
+        if (!std::isfinite(gle->a_p[k]) || !std::isfinite(gle->c_p[k]))
+            return fail(msg, FTH_E_INVALID_ARG, "A_p / C_p not finite");
+        x[k] = -0.5 * dt * gle->a_p[k];
+    }
+    mat_exp(ns, x.data(), T);
+    // C_p - T C_p T^T
+    mat_mul(ns, T, gle->c_p, tmp.data());
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j) tt[i * ns + j] = T[j * ns + i];
+    mat_mul(ns, tmp.data(), tt.data(), tct.data());
+    for (int k = 0; k < ns * ns; ++k) tct[k] = gle->c_p[k] - tct[k];
+    for (int i = 0; i < ns; ++i)
+        if (tct[i * ns + i] < -1e-12 * std::max(1.0, std::fabs(gle->c_p[i * ns + i])))
+            return fail(msg, FTH_E_INVALID_ARG,
+                        "C_p - T C_p T^T is not positive semi-definite (invalid GLE)");
+    chol_psd(ns, tct.data(), S);
+    for (int k = 0; k < ns * ns; ++k)
+        if (!std::isfinite(T[k]) || !std::isfinite(S[k]))
+            return fail(msg, FTH_E_INVALID_ARG, "propagator not finite");
+    return FTH_OK;
+}
+
+// ------------------------------------------------------------------ validation + layout
+fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, Layout* L,
+                std::string* msg) {
+    if (!M || !gle || !o || !L) return fail(msg, FTH_E_INVALID_ARG, "NULL argument");
+    if (M->n < 1 || M->n > (1ll << 30)) return fail(msg, FTH_E_INVALID_ARG, "n out of range");
+    if (!M->values) return fail(msg, FTH_E_INVALID_ARG, "matrix values are NULL");
+    if (M->dtype != FTH_F32 && M->dtype != FTH_F64) return fail(msg, FTH_E_INVALID_ARG, "bad dtype");
+    if (M->kind != FTH_DENSE && M->kind != FTH_CSR) return fail(msg, FTH_E_INVALID_ARG, "bad kind");
+    if (gle->s < 0 || gle->s > 4) return fail(msg, FTH_E_UNSUPPORTED, "s must be in [0, 4]");
+    if (o->replicas < 1 || o->replicas > (1ll << 24))
+        return fail(msg, FTH_E_INVALID_ARG, "replicas out of range");
+    if (!(o->dt > 0.0)) return fail(msg, FTH_E_INVALID_ARG, "dt must be > 0");
+    if (o->block < 1 || o->burnin < 0) return fail(msg, FTH_E_INVALID_ARG, "block >= 1, burnin >= 0");
+    if (o->observable != FTH_OBS_P && o->observable != FTH_OBS_Q)
+        return fail(msg, FTH_E_INVALID_ARG, "bad observable");
+    if (o->precision < FTH_PREC_FP32 || o->precision > FTH_PREC_FP64)
+        return fail(msg, FTH_E_INVALID_ARG, "bad precision");
+    if (o->track < FTH_TRACK_LIST || o->track > FTH_TRACK_ALL)
+        return fail(msg, FTH_E_INVALID_ARG, "bad track");
+    if (o->track == FTH_TRACK_LIST && (o->npairs < 0 || (o->npairs > 0 && !o->pairs)))
+        return fail(msg, FTH_E_INVALID_ARG, "pairs");
+    if (o->stack < 0) return fail(msg, FTH_E_INVALID_ARG, "stack must be >= 0");
+
+    *L = Layout();
+    L->ns = gle->s + 1;
+    L->N = M->n;
+    L->R = o->replicas;
+    L->precision = o->precision;
+    L->track = o->track;
+    const bool tc = o->precision == FTH_PREC_TF32 || o->precision == FTH_PREC_BF16X3;
+    if (M->kind == FTH_CSR) {
+        if (o->precision != FTH_PREC_FP32)
+            return fail(msg, FTH_E_UNSUPPORTED, "CSR matrices use the FP32 SpMM path");
+        if (o->track == FTH_TRACK_ALL)
+            return fail(msg, FTH_E_UNSUPPORTED, "track ALL is for dense matrices");
+        if (!M->rowptr || !M->colind || M->nnz < 0)
+            return fail(msg, FTH_E_INVALID_ARG, "CSR arrays");
+        L->path = kPathCsr;
+        L->nnz = M->nnz;
+        L->Np = L->N;
+    } else if (o->precision == FTH_PREC_FP64) {
+        if (M->n > 1024) return fail(msg, FTH_E_UNSUPPORTED, "FP64 path supports n <= 1024");
+        L->path = kPathDense64;
+        L->Np = round_up(L->N, 32);
+    } else {
+        L->path = kPathDense32;
+        L->Np = round_up(L->N, kTile);
+    }
+    // replicas padded to a float4 (element-wise kernels); the tensor-core paths pad to
+    // the 64-wide force tile so TMA boxes never exceed the tensor and every staged
+    // SYRK slice of 32 columns holds whole samples
+    L->Rp = round_up(L->R, tc ? 64 : 4);
+
+    // tracked elements
+    int64_t ntracked = 0;
+    if (L->path == kPathDense64) {
+        if (o->track == FTH_TRACK_LIST) ntracked = o->npairs;
+        else if (o->track == FTH_TRACK_DIAG) ntracked = L->N;
+        else ntracked = L->N * (L->N + 1) / 2;
+    } else if (o->track == FTH_TRACK_LIST) {
+        ntracked = o->npairs;
+    } else if (o->track == FTH_TRACK_DIAG) {
+        ntracked = L->N;
+    }
+    L->ntracked = ntracked;
+    const bool all32 = L->path == kPathDense32 && o->track == FTH_TRACK_ALL;
+    L->nbt = all32 ? L->Np / kTile : 0;
+    L->count = all32 ? (L->nbt * (L->nbt + 1) / 2) * kTile * kTile : ntracked;
+    if (o->track == FTH_TRACK_LIST && o->pairs) {
+        for (int64_t e = 0; e < o->npairs; ++e) {
+            const int64_t i = o->pairs[2 * e], j = o->pairs[2 * e + 1];
+            if (i < 0 || j < 0 || i >= L->N || j >= L->N)
+                return fail(msg, FTH_E_INVALID_ARG, "pair index out of range");
+        }
+    }
+    if (L->path != kPathDense64) {
+        L->stack = o->stack > 0 ? o->stack
+                                : (all32 ? std::max<int64_t>(1, 2048 / L->Rp) : 4);
+        L->ps_ld = L->stack * L->Rp;
+    }
+
+    // workspace carving
+    Carve c;
+    const int64_t N = L->N, Np = L->Np, Rp = L->Rp;
+    const int nsub = L->ns - 1;
+    if (L->path == kPathDense32) {
+        const size_t esz = o->precision == FTH_PREC_BF16X3 ? 2 : 4;
+        L->off_M = c.take((size_t)Np * Np * esz);
+        if (o->precision == FTH_PREC_BF16X3) L->off_Mlo = c.take((size_t)Np * Np * esz);
+        L->off_q0 = c.take((size_t)Np * Rp * 4);
+        L->off_p = c.take((size_t)Np * Rp * 4);
+        L->off_s = c.take((size_t)std::max(nsub, 1) * Np * Rp * 4);
+        L->off_MQ = c.take((size_t)Np * Rp * 4);
+        if (tc) {
+            L->off_ophi = c.take((size_t)Rp * Np * esz);
+            if (o->precision == FTH_PREC_BF16X3) L->off_oplo = c.take((size_t)Rp * Np * esz);
+        }
+        L->off_ps = c.take((size_t)Np * L->ps_ld * 4);
+    } else if (L->path == kPathCsr) {
+        L->off_rowptr = c.take((size_t)(N + 1) * 4);
+        L->off_col = c.take((size_t)std::max<int64_t>(L->nnz, 1) * 4);
+        L->off_val = c.take((size_t)std::max<int64_t>(L->nnz, 1) * 4);
+        L->off_q0 = c.take((size_t)N * Rp * 4);
+        L->off_q1 = c.take((size_t)N * Rp * 4);
+        L->off_p = c.take((size_t)N * Rp * 4);
+        L->off_s = c.take((size_t)std::max(nsub, 1) * N * Rp * 4);
+        L->off_ps = c.take((size_t)N * L->ps_ld * 4);
+    } else {
+        L->off_M = c.take((size_t)N * Np * 8);
+        L->off_q0 = c.take((size_t)L->R * Np * 8);
+        L->off_p = c.take((size_t)L->R * Np * 8);
+        L->off_s = c.take((size_t)std::max(nsub, 1) * L->R * Np * 8);
+    }
+    L->off_pairs = c.take((size_t)std::max<int64_t>(ntracked, 1) * 2 * 4);
+    if (L->path == kPathDense64) L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * L->R * 8);
+    else L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * 4);
+    L->off_mean = c.take((size_t)std::max<int64_t>(L->count, 1) * 8);
+    L->off_m2 = c.take((size_t)std::max<int64_t>(L->count, 1) * 8);
+    L->off_gidx = c.take((size_t)kGatherChunk * 8);
+    L->off_gout = c.take((size_t)kGatherChunk * 3 * 8);
+    L->off_err = c.take(256);
+    L->total = c.off;
+    return FTH_OK;
+}
+
+inline uint16_t bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);  // inf / nan
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+inline float bf16_to_f(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+inline float tf32_rna(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) != 0x7F800000u) {
+        u += 0x1000u;
+        u &= ~0x1FFFu;
+    }
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+}  // namespace
+
+// ======================================================================== context
+struct fth_ctx {
+    Layout L;
+    cudaStream_t stream = nullptr;
+    int observable = 0;
+    int64_t burnin = 0, block = 1;
+    uint64_t seed = 0;
+    double dt = 0;
+    double T[kMaxNs * kMaxNs] = {}, S[kMaxNs * kMaxNs] = {};
+    GleF32 g32{};
+    GleF64 g64{};
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+    // device pointers
+    void* M = nullptr;
+    void* Mlo = nullptr;
+    int32_t *rowptr = nullptr, *col = nullptr;
+    float* val = nullptr;
+    void* q[2] = {nullptr, nullptr};
+    void *p = nullptr, *s = nullptr;
+    float* MQ = nullptr;
+    void *ophi = nullptr, *oplo = nullptr;
+    float* ps = nullptr;
+    int32_t* pairs = nullptr;
+    void* partial = nullptr;
+    double *mean = nullptr, *m2 = nullptr;
+    int64_t* gidx = nullptr;
+    double* gout = nullptr;
+    uint32_t* err = nullptr;
+    TcForce* tcf = nullptr;
+    TcSyrk* tcs = nullptr;
+    // host-side bookkeeping
+    std::unordered_map<uint64_t, int64_t> pair_index;
+    int64_t t = 0, nsamp = 0, accumulated = 0, inblock = 0, nfill = 0, nblocks = 0, launches = 0;
+    int primed = 0, cur = 0;
+    std::string last_error;
+};
+
+namespace {
+
+uint64_t pair_key(int64_t i, int64_t j) {
+    if (i > j) std::swap(i, j);
+    return ((uint64_t)i << 32) | (uint64_t)j;
+}
+
+fth_status cuda_fail(fth_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (c) c->last_error = m;
+    else g_thread_error = m;
+    return FTH_E_CUDA;
+}
+
+#define FTH_CK(call, what)                                 \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+bool is_tc(const fth_ctx* c) {
+    return c->L.path == kPathDense32 &&
+           (c->L.precision == FTH_PREC_TF32 || c->L.precision == FTH_PREC_BF16X3);
+}
+
+fth_status force(fth_ctx* c) {
+    const Layout& L = c->L;
+    if (is_tc(c)) {
+        FTH_CK(tc_force_run(c->tcf, c->MQ, L.Rp, c->err, c->stream), "tc force");
+    } else {
+        FTH_CK(launch_sgemm_force(static_cast<const float*>(c->M), L.Np,
+                                  static_cast<const float*>(c->q[0]), L.Rp, c->MQ, L.N, c->stream),
+               "sgemm force");
+    }
+    ++c->launches;
+    return FTH_OK;
+}
+
+fth_status accumulate(fth_ctx* c) {
+    const Layout& L = c->L;
+    if (c->nfill == 0) return FTH_OK;
+    const int64_t ncols = c->nfill * L.Rp;
+    if (L.track == FTH_TRACK_ALL) {
+        if (is_tc(c)) {
+            FTH_CK(tc_syrk_run(c->tcs, ncols, static_cast<float*>(c->partial), c->err, c->stream),
+                   "tc syrk");
+        } else {
+            FTH_CK(launch_syrk_fp32(c->ps, L.ps_ld, ncols, L.Np, static_cast<float*>(c->partial),
+                                    c->stream),
+                   "syrk");
+        }
+    } else {
+        FTH_CK(launch_pair_accum(c->ps, L.ps_ld, ncols, c->pairs, L.ntracked,
+                                 static_cast<float*>(c->partial), c->stream),
+               "pair accumulate");
+    }
+    ++c->launches;
+    c->nfill = 0;
+    return FTH_OK;
+}
+
+fth_status flush(fth_ctx* c) {
+    const Layout& L = c->L;
+    const double inv = 1.0 / ((double)c->block * (double)L.R);
+    const double nb = (double)(c->nblocks + 1);
+    if (L.path == kPathDense64) {
+        FTH_CK(launch_flush64(static_cast<double*>(c->partial), L.R, L.count, c->mean, c->m2,
+                              L.count, inv, nb, c->err, c->stream),
+               "flush64");
+    } else {
+        FTH_CK(launch_flush(static_cast<float*>(c->partial), c->mean, c->m2, L.count, inv, nb,
+                            c->err, c->stream),
+               "flush");
+    }
+    ++c->launches;
+    ++c->nblocks;
+    c->inblock = 0;
+    return FTH_OK;
+}
+
+void op_ptrs(fth_ctx* c, int& kind, void*& hi, void*& lo) {
+    kind = kOpNone;
+    hi = lo = nullptr;
+    if (c->L.path != kPathDense32) return;
+    if (c->L.precision == FTH_PREC_TF32) kind = kOpTf32;
+    if (c->L.precision == FTH_PREC_BF16X3) kind = kOpBf16x2;
+    hi = c->ophi;
+    lo = c->oplo;
+}
+
+fth_status run_dense32(fth_ctx* c, int64_t steps) {
+    const Layout& L = c->L;
+    int opk;
+    void *hi, *lo;
+    op_ptrs(c, opk, hi, lo);
+    float* q = static_cast<float*>(c->q[0]);
+    float* p = static_cast<float*>(c->p);
+    float* s = static_cast<float*>(c->s);
+    if (!c->primed) {
+        fth_status st = force(c);
+        if (st != FTH_OK) return st;
+        FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s, (uint32_t)c->t,
+                                kDoStart, c->observable, c->ps, L.ps_ld, 0, opk, hi, lo, L.Np,
+                                c->stream),
+               "gle prologue");
+        ++c->launches;
+        c->primed = 1;
+    }
+    for (int64_t k = 0; k < steps; ++k) {
+        fth_status st = force(c);
+        if (st != FTH_OK) return st;
+        const bool take = c->nsamp >= c->burnin;
+        const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0);
+        FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s,
+                                (uint32_t)(c->t + 1), flags, c->observable, c->ps, L.ps_ld,
+                                c->nfill, opk, hi, lo, L.Np, c->stream),
+               "gle step");
+        ++c->launches;
+        ++c->t;
+        ++c->nsamp;
+        if (take) {
+            ++c->nfill;
+            ++c->inblock;
+            ++c->accumulated;
+            if (c->nfill == L.stack || c->inblock == c->block) {
+                st = accumulate(c);
+                if (st != FTH_OK) return st;
+            }
+            if (c->inblock == c->block) {
+                st = flush(c);
+                if (st != FTH_OK) return st;
+            }
+        }
+    }
+    return accumulate(c);
+}
+
+fth_status run_csr(fth_ctx* c, int64_t steps) {
+    const Layout& L = c->L;
+    float* p = static_cast<float*>(c->p);
+    float* s = static_cast<float*>(c->s);
+    auto launch = [&](int flags, uint32_t kappa) -> fth_status {
+        float* qin = static_cast<float*>(c->q[c->cur]);
+        float* qout = static_cast<float*>(c->q[c->cur ^ 1]);
+        FTH_CK(launch_csr_step(L.ns, c->g32, L.N, L.R, L.Rp, c->rowptr, c->col, c->val, qin, qout,
+                               p, s, kappa, flags, c->observable, c->ps, L.ps_ld, c->nfill,
+                               c->stream),
+               "csr step");
+        ++c->launches;
+        c->cur ^= 1;
+        return FTH_OK;
+    };
+    if (!c->primed) {
+        fth_status st = launch(kDoStart, (uint32_t)c->t);
+        if (st != FTH_OK) return st;
+        c->primed = 1;
+    }
+    for (int64_t k = 0; k < steps; ++k) {
+        const bool take = c->nsamp >= c->burnin;
+        fth_status st = launch(kDoEnd | kDoStart | (take ? kDoSample : 0), (uint32_t)(c->t + 1));
+        if (st != FTH_OK) return st;
+        ++c->t;
+        ++c->nsamp;
+        if (take) {
+            ++c->nfill;
+            ++c->inblock;
+            ++c->accumulated;
+            if (c->nfill == L.stack || c->inblock == c->block) {
+                st = accumulate(c);
+                if (st != FTH_OK) return st;
+            }
+            if (c->inblock == c->block) {
+                st = flush(c);
+                if (st != FTH_OK) return st;
+            }
+        }
+    }
+    return accumulate(c);
+}
+
+fth_status run_dense64(fth_ctx* c, int64_t steps) {
+    const Layout& L = c->L;
+    while (steps > 0 || !c->primed) {
+        // one segment: up to the end of the current block (or the burn-in), in one launch
+        int64_t seg = steps;
+        int64_t acc_from = 0;
+        if (c->nsamp < c->burnin) {
+            acc_from = c->burnin - c->nsamp;
+            seg = std::min(seg, acc_from + (c->block - c->inblock));
+        } else {
+            seg = std::min(seg, c->block - c->inblock);
+        }
+        seg = std::min<int64_t>(seg, 1 << 20);
+        const uint32_t kappa0 = (uint32_t)(c->primed ? c->t + 1 : c->t);
+        FTH_CK(launch_fp64_dense(L.ns, c->g64, L.N, L.Np, L.R, static_cast<const double*>(c->M),
+                                 static_cast<double*>(c->q[0]), static_cast<double*>(c->p),
+                                 static_cast<double*>(c->s), kappa0, seg, c->primed,
+                                 c->observable, c->pairs, L.ntracked,
+                                 static_cast<double*>(c->partial), acc_from, c->stream),
+               "fp64 dense");
+        ++c->launches;
+        c->primed = 1;
+        c->t += seg;
+        c->nsamp += seg;
+        const int64_t took = std::max<int64_t>(0, seg - acc_from);
+        c->inblock += took;
+        c->accumulated += took;
+        steps -= seg;
+        if (c->inblock == c->block) {
+            fth_status st = flush(c);
+            if (st != FTH_OK) return st;
+        }
+        if (seg == 0 && steps == 0) break;
+    }
+    return FTH_OK;
+}
+
+fth_status upload_state_operand(fth_ctx* c) {
+    // refresh the transposed force operand from the FP32 q plane (TC paths)
+    const Layout& L = c->L;
+    if (!is_tc(c)) return FTH_OK;
+    std::vector<float> q((size_t)L.Np * L.Rp);
+    FTH_CK(cudaMemcpyAsync(q.data(), c->q[0], q.size() * 4, cudaMemcpyDeviceToHost, c->stream),
+           "d2h q");
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    if (L.precision == FTH_PREC_TF32) {
+        std::vector<float> t((size_t)L.Rp * L.Np, 0.f);
+        for (int64_t i = 0; i < L.N; ++i)
+            for (int64_t r = 0; r < L.Rp; ++r) t[r * L.Np + i] = tf32_rna(q[i * L.Rp + r]);
+        FTH_CK(cudaMemcpyAsync(c->ophi, t.data(), t.size() * 4, cudaMemcpyHostToDevice, c->stream),
+               "h2d op");
+    } else {
+        std::vector<uint16_t> h((size_t)L.Rp * L.Np, 0), l((size_t)L.Rp * L.Np, 0);
+        for (int64_t i = 0; i < L.N; ++i)
+            for (int64_t r = 0; r < L.Rp; ++r) {
+                const float x = q[i * L.Rp + r];
+                const uint16_t hb = bf16_rne(x);
+                h[r * L.Np + i] = hb;
+                l[r * L.Np + i] = bf16_rne(x - bf16_to_f(hb));
+            }
+        FTH_CK(cudaMemcpyAsync(c->ophi, h.data(), h.size() * 2, cudaMemcpyHostToDevice, c->stream),
+               "h2d op hi");
+        FTH_CK(cudaMemcpyAsync(c->oplo, l.data(), l.size() * 2, cudaMemcpyHostToDevice, c->stream),
+               "h2d op lo");
+    }
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    return FTH_OK;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+const char* fth_version(void) { return "fth 0.1 (sm_103a)"; }
+
+const char* fth_last_error(const fth_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : g_thread_error.c_str();
+}
+
+fth_status fth_gle_propagator(const fth_gle* gle, double dt, double* T, double* S) {
+    if (!T || !S) return fail(nullptr, FTH_E_INVALID_ARG, "NULL output");
+    return propagator(gle, dt, T, S, nullptr);
+}
+
+fth_status fth_workspace_size(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
+                              size_t* bytes) {
+    if (!bytes) return fail(nullptr, FTH_E_INVALID_ARG, "bytes is NULL");
+    Layout L;
+    fth_status st = plan(M, gle, opt, &L, nullptr);
+    if (st != FTH_OK) return st;
+    *bytes = L.total;
+    return FTH_OK;
+}
+
+fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_options* opt,
+                      void* workspace, size_t workspace_bytes, fth_ctx** out) {
+    if (!out) return fail(nullptr, FTH_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    Layout L;
+    fth_status st = plan(Min, gle, opt, &L, nullptr);
+    if (st != FTH_OK) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return fail(nullptr, FTH_E_WORKSPACE, "workspace must be 256-byte aligned device memory");
+    if (workspace_bytes < L.total)
+        return fail(nullptr, FTH_E_WORKSPACE, "workspace too small: need " + std::to_string(L.total) +
+                                                  " bytes");
+    fth_ctx* c = new fth_ctx();
+    c->L = L;
+    c->stream = static_cast<cudaStream_t>(opt->stream);
+    c->observable = opt->observable;
+    c->burnin = opt->burnin;
+    c->block = opt->block;
+    c->seed = opt->seed;
+    c->dt = opt->dt;
+    c->ws = static_cast<uint8_t*>(workspace);
+    c->ws_bytes = workspace_bytes;
+    st = propagator(gle, opt->dt, c->T, c->S, &c->last_error);
+    if (st != FTH_OK) {
+        g_thread_error = c->last_error;
+        delete c;
+        return st;
+    }
+    const int ns = L.ns;
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            c->g32.T[a * kMaxNs + b] = (float)c->T[a * ns + b];
+            c->g32.S[a * kMaxNs + b] = (float)c->S[a * ns + b];
+            c->g64.T[a * kMaxNs + b] = c->T[a * ns + b];
+            c->g64.S[a * kMaxNs + b] = c->S[a * ns + b];
+        }
+    c->g32.dt = (float)opt->dt;
+    c->g32.hdt = (float)(0.5 * opt->dt);
+    c->g64.dt = opt->dt;
+    c->g64.hdt = 0.5 * opt->dt;
+    c->g32.key0 = c->g64.key0 = (uint32_t)opt->seed;
+    c->g32.key1 = c->g64.key1 = (uint32_t)(opt->seed >> 32);
+
+    auto at = [&](size_t off) { return static_cast<void*>(c->ws + off); };
+    c->M = at(L.off_M);
+    c->Mlo = L.off_Mlo ? at(L.off_Mlo) : nullptr;
+    c->q[0] = at(L.off_q0);
+    c->q[1] = L.off_q1 ? at(L.off_q1) : nullptr;
+    c->p = at(L.off_p);
+    c->s = at(L.off_s);
+    c->MQ = L.off_MQ ? static_cast<float*>(at(L.off_MQ)) : nullptr;
+    c->ophi = L.off_ophi ? at(L.off_ophi) : nullptr;
+    c->oplo = L.off_oplo ? at(L.off_oplo) : nullptr;
+    c->ps = L.off_ps ? static_cast<float*>(at(L.off_ps)) : nullptr;
+    c->pairs = static_cast<int32_t*>(at(L.off_pairs));
+    c->partial = at(L.off_partial);
+    c->mean = static_cast<double*>(at(L.off_mean));
+    c->m2 = static_cast<double*>(at(L.off_m2));
+    c->gidx = static_cast<int64_t*>(at(L.off_gidx));
+    c->gout = static_cast<double*>(at(L.off_gout));
+    c->err = static_cast<uint32_t*>(at(L.off_err));
+    if (L.path == kPathCsr) {
+        c->rowptr = static_cast<int32_t*>(at(L.off_rowptr));
+        c->col = static_cast<int32_t*>(at(L.off_col));
+        c->val = static_cast<float*>(at(L.off_val));
+    }
+
+    auto bail = [&](fth_status s2) {
+        g_thread_error = c->last_error;
+        if (c->tcf) tc_force_free(c->tcf);
+        if (c->tcs) tc_syrk_free(c->tcs);
+        delete c;
+        return s2;
+    };
+#define FTH_CK_C(call, what)                                \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, what)); \
+    } while (0)
+
+    FTH_CK_C(cudaMemsetAsync(c->ws, 0, L.total, c->stream), "zero workspace");
+
+    // ---- M: bring to host FP64 (validation, conversion), then upload
+    const int64_t N = L.N;
+    const size_t esz_in = Min->dtype == FTH_F64 ? 8 : 4;
+    if (Min->kind == FTH_DENSE) {
+        std::vector<double> m((size_t)N * N);
+        {
+            std::vector<uint8_t> raw((size_t)N * N * esz_in);
+            if (Min->on_device) {
+                FTH_CK_C(cudaMemcpy(raw.data(), Min->values, raw.size(), cudaMemcpyDeviceToHost), "d2h M");
+            } else {
+                std::memcpy(raw.data(), Min->values, raw.size());
+            }
+            for (size_t k = 0; k < m.size(); ++k)
+                m[k] = esz_in == 8 ? reinterpret_cast<const double*>(raw.data())[k]
+                                   : (double)reinterpret_cast<const float*>(raw.data())[k];
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            if (!(m[i * N + i] > 0.0)) {
+                c->last_error = "M has a non-positive diagonal entry: not positive definite";
+                return bail(FTH_E_NOT_SPD);
+            }
+        }
+        for (double x : m)
+            if (!std::isfinite(x)) {
+                c->last_error = "M has non-finite entries";
+                return bail(FTH_E_INVALID_ARG);
+            }
+        const int64_t Np = L.Np;
+        if (L.path == kPathDense64) {
+            std::vector<double> h((size_t)N * Np, 0.0);
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = 0; j < N; ++j) h[i * Np + j] = m[i * N + j];
+            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream), "h2d M");
+            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        } else if (L.precision == FTH_PREC_BF16X3) {
+            std::vector<uint16_t> h((size_t)Np * Np, 0), l((size_t)Np * Np, 0);
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = 0; j < N; ++j) {
+                    const float x = (float)m[i * N + j];
+                    const uint16_t hb = bf16_rne(x);
+                    h[i * Np + j] = hb;
+                    l[i * Np + j] = bf16_rne(x - bf16_to_f(hb));
+                }
+            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M hi");
+            FTH_CK_C(cudaMemcpyAsync(c->Mlo, l.data(), l.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M lo");
+            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        } else {
+            std::vector<float> h((size_t)Np * Np, 0.f);
+            const bool tf = L.precision == FTH_PREC_TF32;
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = 0; j < N; ++j) {
+                    const float x = (float)m[i * N + j];
+                    h[i * Np + j] = tf ? tf32_rna(x) : x;
+                }
+            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d M");
+            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        }
+    } else {
+        const int64_t nnz = L.nnz;
+        std::vector<int32_t> rp(N + 1), ci(std::max<int64_t>(nnz, 1));
+        std::vector<uint8_t> raw((size_t)std::max<int64_t>(nnz, 1) * esz_in);
+        if (Min->on_device) {
+            FTH_CK_C(cudaMemcpy(rp.data(), Min->rowptr, (N + 1) * 4, cudaMemcpyDeviceToHost), "d2h rowptr");
+            if (nnz) {
+                FTH_CK_C(cudaMemcpy(ci.data(), Min->colind, nnz * 4, cudaMemcpyDeviceToHost), "d2h col");
+                FTH_CK_C(cudaMemcpy(raw.data(), Min->values, nnz * esz_in, cudaMemcpyDeviceToHost), "d2h val");
+            }
+        } else {
+            std::memcpy(rp.data(), Min->rowptr, (N + 1) * 4);
+            if (nnz) {
+                std::memcpy(ci.data(), Min->colind, nnz * 4);
+                std::memcpy(raw.data(), Min->values, nnz * esz_in);
+            }
+        }
+        if (rp[0] != 0 || rp[N] != nnz) {
+            c->last_error = "CSR rowptr must start at 0 and end at nnz";
+            return bail(FTH_E_INVALID_ARG);
+        }
+        std::vector<float> v(std::max<int64_t>(nnz, 1));
+        for (int64_t i = 0; i < N; ++i) {
+            if (rp[i + 1] < rp[i]) {
+                c->last_error = "CSR rowptr not non-decreasing";
+                return bail(FTH_E_INVALID_ARG);
+            }
+            bool diag = false;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                if (ci[e] < 0 || ci[e] >= N) {
+                    c->last_error = "CSR column index out of range";
+                    return bail(FTH_E_INVALID_ARG);
+                }
+                const double x = esz_in == 8 ? reinterpret_cast<const double*>(raw.data())[e]
+                                             : (double)reinterpret_cast<const float*>(raw.data())[e];
+                if (!std::isfinite(x)) {
+                    c->last_error = "CSR values not finite";
+                    return bail(FTH_E_INVALID_ARG);
+                }
+                v[e] = (float)x;
+                if (ci[e] == i && x > 0.0) diag = true;
+            }
+            if (!diag) {
+                c->last_error = "CSR row without a positive diagonal entry: not positive definite";
+                return bail(FTH_E_NOT_SPD);
+            }
+        }
+        FTH_CK_C(cudaMemcpyAsync(c->rowptr, rp.data(), (N + 1) * 4, cudaMemcpyHostToDevice, c->stream), "h2d rowptr");
+        FTH_CK_C(cudaMemcpyAsync(c->col, ci.data(), std::max<int64_t>(nnz, 1) * 4, cudaMemcpyHostToDevice, c->stream), "h2d col");
+        FTH_CK_C(cudaMemcpyAsync(c->val, v.data(), std::max<int64_t>(nnz, 1) * 4, cudaMemcpyHostToDevice, c->stream), "h2d val");
+        FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+    }
+
+    // ---- tracked pairs
+    {
+        std::vector<int32_t> pr;
+        pr.reserve((size_t)L.ntracked * 2);
+        auto add = [&](int64_t i, int64_t j) {
+            if (i > j) std::swap(i, j);
+            const int64_t idx = (int64_t)pr.size() / 2;
+            c->pair_index.emplace(pair_key(i, j), idx);
+            pr.push_back((int32_t)i);
+            pr.push_back((int32_t)j);
+        };
+        if (L.track == FTH_TRACK_LIST) {
+            for (int64_t e = 0; e < opt->npairs; ++e) add(opt->pairs[2 * e], opt->pairs[2 * e + 1]);
+        } else if (L.track == FTH_TRACK_DIAG) {
+            for (int64_t i = 0; i < N; ++i) add(i, i);
+        } else if (L.path == kPathDense64) {
+            for (int64_t i = 0; i < N; ++i)
+                for (int64_t j = i; j < N; ++j) add(i, j);
+        }
+        if (!pr.empty()) {
+            FTH_CK_C(cudaMemcpyAsync(c->pairs, pr.data(), pr.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d pairs");
+            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        }
+    }
+
+    // ---- tensor maps
+    if (is_tc(c)) {
+        const int kind = L.precision == FTH_PREC_TF32 ? 1 : 2;
+        FTH_CK_C(tc_force_prepare(&c->tcf, kind, c->M, c->Mlo, c->ophi, c->oplo, L.Np, L.Rp, L.N, L.R),
+                 "tensor maps (force)");
+        if (L.track == FTH_TRACK_ALL)
+            FTH_CK_C(tc_syrk_prepare(&c->tcs, c->ps, L.Np, L.ps_ld), "tensor maps (syrk)");
+    }
+#undef FTH_CK_C
+    *out = c;
+    return FTH_OK;
+}
+
+fth_status fth_run(fth_ctx* c, int64_t steps) {
+    if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
+    if (steps < 0) {
+        c->last_error = "steps must be >= 0";
+        return FTH_E_INVALID_ARG;
+    }
+    if (c->t + steps + 2 > (int64_t)0xFFFFFFFFll) {
+        c->last_error = "kick index would exceed 2^32";
+        return FTH_E_INVALID_ARG;
+    }
+    switch (c->L.path) {
+        case kPathDense32: return run_dense32(c, steps);
+        case kPathCsr: return run_csr(c, steps);
+        default: return run_dense64(c, steps);
+    }
+}
+
+fth_status fth_status_poll(fth_ctx* c) {
+    if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
+    uint32_t e = 0;
+    FTH_CK(cudaMemcpyAsync(&e, c->err, 4, cudaMemcpyDeviceToHost, c->stream), "d2h err");
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    if (e & kErrTimeout) {
+        c->last_error = "a device wait timed out";
+        return FTH_E_TIMEOUT;
+    }
+    if (e & kErrNonFinite) {
+        c->last_error = "non-finite accumulator at a block flush";
+        return FTH_E_NONFINITE;
+    }
+    return FTH_OK;
+}
+
+fth_status fth_elements(fth_ctx* c, const int64_t* pairs, int64_t k, double* values,
+                        double* errbars) {
+    if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
+    if (k < 0 || (k > 0 && (!pairs || !values))) {
+        c->last_error = "bad pairs / values";
+        return FTH_E_INVALID_ARG;
+    }
+    fth_status st = fth_status_poll(c);
+    if (st != FTH_OK) return st;
+    const Layout& L = c->L;
+    std::vector<int64_t> idx((size_t)k);
+    for (int64_t e = 0; e < k; ++e) {
+        const int64_t i = pairs[2 * e], j = pairs[2 * e + 1];
+        if (i < 0 || j < 0 || i >= L.N || j >= L.N) {
+            c->last_error = "pair index out of range";
+            return FTH_E_INVALID_ARG;
+        }
+        if (L.track == FTH_TRACK_ALL && L.path == kPathDense32) {
+            idx[e] = packed_index(i, j, L.nbt);
+        } else {
+            auto it = c->pair_index.find(pair_key(i, j));
+            if (it == c->pair_index.end()) {
+                c->last_error = "element (" + std::to_string(i) + ", " + std::to_string(j) +
+                                ") is not tracked";
+                return FTH_E_NOT_TRACKED;
+            }
+            idx[e] = it->second;
+        }
+    }
+    const double nb = (double)c->nblocks;
+    const double nacc = (double)(c->nblocks * c->block + c->inblock);
+    std::vector<double> out((size_t)kGatherChunk * 3);
+    for (int64_t b0 = 0; b0 < k; b0 += kGatherChunk) {
+        const int64_t m = std::min(kGatherChunk, k - b0);
+        FTH_CK(cudaMemcpyAsync(c->gidx, idx.data() + b0, m * 8, cudaMemcpyHostToDevice, c->stream),
+               "h2d idx");
+        const bool p64 = L.path == kPathDense64;
+        FTH_CK(launch_gather(c->gidx, m, c->mean, c->m2,
+                             p64 ? nullptr : static_cast<const float*>(c->partial),
+                             p64 ? static_cast<const double*>(c->partial) : nullptr, L.R, L.count,
+                             c->gout, c->stream),
+               "gather");
+        FTH_CK(cudaMemcpyAsync(out.data(), c->gout, m * 3 * 8, cudaMemcpyDeviceToHost, c->stream),
+               "d2h gather");
+        FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+        for (int64_t e = 0; e < m; ++e) {
+            const double mean = out[3 * e], m2 = out[3 * e + 1], part = out[3 * e + 2];
+            const double total = mean * nb * (double)c->block * (double)L.R + part;
+            values[b0 + e] = nacc > 0 ? total / (nacc * (double)L.R) : NAN;
+            if (errbars) errbars[b0 + e] = nb >= 2 ? std::sqrt(m2 / (nb * (nb - 1.0))) : NAN;
+        }
+    }
+    return FTH_OK;
+}
+
+fth_status fth_get_state(fth_ctx* c, int plane, double* host) {
+    if (!c || !host) return fail(nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    const Layout& L = c->L;
+    const int nsub = L.ns - 1;
+    if (plane < FTH_PLANE_Q || plane > FTH_PLANE_S) {
+        c->last_error = "bad plane";
+        return FTH_E_INVALID_ARG;
+    }
+    const int nplanes = plane == FTH_PLANE_S ? nsub : 1;
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    for (int a = 0; a < nplanes; ++a) {
+        if (L.path == kPathDense64) {
+            const double* src = static_cast<const double*>(
+                plane == FTH_PLANE_Q ? c->q[0] : plane == FTH_PLANE_P ? c->p : c->s);
+            src += (size_t)a * L.R * L.Np;
+            std::vector<double> h((size_t)L.R * L.Np);
+            FTH_CK(cudaMemcpy(h.data(), src, h.size() * 8, cudaMemcpyDeviceToHost), "d2h state");
+            for (int64_t r = 0; r < L.R; ++r)
+                for (int64_t i = 0; i < L.N; ++i)
+                    host[((size_t)r * nplanes + a) * L.N + i] = h[r * L.Np + i];
+        } else {
+            const int64_t rows = L.path == kPathCsr ? L.N : L.Np;
+            const float* src = static_cast<const float*>(
+                plane == FTH_PLANE_Q ? c->q[c->cur] : plane == FTH_PLANE_P ? c->p : c->s);
+            src += (size_t)a * rows * L.Rp;
+            std::vector<float> h((size_t)L.N * L.Rp);
+            FTH_CK(cudaMemcpy(h.data(), src, h.size() * 4, cudaMemcpyDeviceToHost), "d2h state");
+            for (int64_t r = 0; r < L.R; ++r)
+                for (int64_t i = 0; i < L.N; ++i)
+                    host[((size_t)r * nplanes + a) * L.N + i] = h[i * L.Rp + r];
+        }
+    }
+    return FTH_OK;
+}
+
+fth_status fth_set_state(fth_ctx* c, int plane, const double* host) {
+    if (!c || !host) return fail(nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    const Layout& L = c->L;
+    const int nsub = L.ns - 1;
+    if (plane < FTH_PLANE_Q || plane > FTH_PLANE_S) {
+        c->last_error = "bad plane";
+        return FTH_E_INVALID_ARG;
+    }
+    const int nplanes = plane == FTH_PLANE_S ? nsub : 1;
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    for (int a = 0; a < nplanes; ++a) {
+        if (L.path == kPathDense64) {
+            double* dst = static_cast<double*>(
+                plane == FTH_PLANE_Q ? c->q[0] : plane == FTH_PLANE_P ? c->p : c->s);
+            dst += (size_t)a * L.R * L.Np;
+            std::vector<double> h((size_t)L.R * L.Np, 0.0);
+            for (int64_t r = 0; r < L.R; ++r)
+                for (int64_t i = 0; i < L.N; ++i) h[r * L.Np + i] = host[((size_t)r * nplanes + a) * L.N + i];
+            FTH_CK(cudaMemcpy(dst, h.data(), h.size() * 8, cudaMemcpyHostToDevice), "h2d state");
+        } else {
+            const int64_t rows = L.path == kPathCsr ? L.N : L.Np;
+            float* dst = static_cast<float*>(
+                plane == FTH_PLANE_Q ? c->q[c->cur] : plane == FTH_PLANE_P ? c->p : c->s);
+            dst += (size_t)a * rows * L.Rp;
+            std::vector<float> h((size_t)L.N * L.Rp, 0.f);
+            for (int64_t r = 0; r < L.R; ++r)
+                for (int64_t i = 0; i < L.N; ++i) h[i * L.Rp + r] = (float)host[((size_t)r * nplanes + a) * L.N + i];
+            FTH_CK(cudaMemcpy(dst, h.data(), h.size() * 4, cudaMemcpyHostToDevice), "h2d state");
+        }
+    }
+    if (plane == FTH_PLANE_Q) return upload_state_operand(c);
+    return FTH_OK;
+}
+
+fth_status fth_info(const fth_ctx* c, fth_info_t* info) {
+    if (!c || !info) return fail(nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    info->steps = c->t;
+    info->samples = c->nsamp;
+    info->accumulated = c->accumulated;
+    info->blocks = c->nblocks;
+    info->launches = c->launches;
+    info->primed = c->primed;
+    info->precision = c->L.precision;
+    info->n = c->L.N;
+    info->replicas = c->L.R;
+    info->tracked = c->L.count;
+    info->workspace_bytes = c->L.total;
+    return FTH_OK;
+}
+
+void fth_destroy(fth_ctx* c) {
+    if (!c) return;
+    if (c->tcf) tc_force_free(c->tcf);
+    if (c->tcs) tc_syrk_free(c->tcs);
+    delete c;
+}
+
+}  // extern "C"

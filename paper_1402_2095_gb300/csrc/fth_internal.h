@@ -1,0 +1,111 @@
+// Internal declarations shared by the host runtime and the kernels of libfth.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fth.h"
+
+namespace fth {
+
+constexpr int kMaxNs = 5;          // s + 1 <= 5 (s <= 4 auxiliary momenta)
+constexpr int kTile = 128;         // tcgen05 M tile (rows per CTA) and SYRK tile edge
+
+// O half-step constants in FP32 (the FP64 originals are built on the host).
+struct GleF32 {
+    float T[kMaxNs * kMaxNs];
+    float S[kMaxNs * kMaxNs];   // lower triangular
+    float dt, hdt;
+    uint32_t key0, key1;
+};
+
+struct GleF64 {
+    double T[kMaxNs * kMaxNs];
+    double S[kMaxNs * kMaxNs];
+    double dt, hdt;
+    uint32_t key0, key1;
+};
+
+// Bits of the device error word.
+enum : uint32_t { kErrTimeout = 1u, kErrNonFinite = 2u };
+
+// Flags of the dense element-wise GLE kernel.
+enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4 };
+
+// Operand copies of q the element-wise kernel writes for the force GEMM.
+enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
+
+// ------------------------------------------------------------------ kernels
+// Dense path, state planes [Np][Rp] FP32 (replica fastest), MQ = M q (positive).
+cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
+                             const float* MQ, float* q, float* p, float* s, uint32_t kappa,
+                             int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
+                             int op_kind, void* op_hi, void* op_lo, int64_t Np,
+                             cudaStream_t st);
+
+cudaError_t launch_sgemm_force(const float* M, int64_t ldm, const float* q, int64_t Rp,
+                               float* MQ, int64_t N, cudaStream_t st);
+
+// CSR path: fused SpMM + GLE (force on q_in, positions written to q_out).
+cudaError_t launch_csr_step(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
+                            const int32_t* rowptr, const int32_t* col, const float* val,
+                            const float* q_in, float* q_out, float* p, float* s,
+                            uint32_t kappa, int flags, int observable, float* ps,
+                            int64_t ps_ld, int64_t slot, cudaStream_t st);
+
+// Accumulation: partial[e] += sum_{c < ncols} ps[i_e][c] * ps[j_e][c].
+cudaError_t launch_pair_accum(const float* ps, int64_t ps_ld, int64_t ncols,
+                              const int32_t* pairs, int64_t npairs, float* partial,
+                              cudaStream_t st);
+
+// SYRK over the staged samples into tile-packed FP32 partials (upper tiles I <= J).
+cudaError_t launch_syrk_fp32(const float* ps, int64_t ps_ld, int64_t ncols, int64_t Np,
+                             float* tiles, cudaStream_t st);
+
+// FP64 Welford update with one block mean per element: b = partial * inv_count.
+cudaError_t launch_flush(float* partial, double* mean, double* m2, int64_t count,
+                         double inv_count, double nb, uint32_t* err, cudaStream_t st);
+cudaError_t launch_flush64(double* partial, int64_t R, int64_t stride, double* mean, double* m2,
+                           int64_t count, double inv_count, double nb, uint32_t* err,
+                           cudaStream_t st);
+
+// Gather (mean, m2, partial) of requested elements into out[3 * k].
+cudaError_t launch_gather(const int64_t* idx, int64_t k, const double* mean, const double* m2,
+                          const float* partial32, const double* partial64, int64_t p64_R,
+                          int64_t p64_stride, double* out, cudaStream_t st);
+
+// Element (i, j) of the tile-packed layout -> flat index (host helper mirrored on device).
+__host__ __device__ inline int64_t packed_index(int64_t i, int64_t j, int64_t nb_tiles) {
+    if (i > j) { int64_t t = i; i = j; j = t; }
+    const int64_t I = i / kTile, J = j / kTile;
+    const int64_t tile = I * nb_tiles - (I * (I - 1)) / 2 + (J - I);
+    return tile * (int64_t)kTile * kTile + (i % kTile) * kTile + (j % kTile);
+}
+
+// Conversions used at create / set_state.
+cudaError_t launch_round_tf32(float* x, int64_t n, cudaStream_t st);
+cudaError_t launch_split_bf16(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);
+
+// FP64 small dense path: one CTA per replica runs `nsteps` fused launches.
+cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
+                              const double* M, double* q, double* p, double* s, uint32_t kappa0,
+                              int64_t nsteps, int primed_in, int observable,
+                              const int32_t* pairs, int64_t npairs, double* partial,
+                              int64_t acc_from, cudaStream_t st);
+
+// tcgen05 / TMA kernels (sm_103a).
+struct TcForce;   // opaque, holds the tensor maps
+cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const void* A_lo,
+                             const void* B_hi, const void* B_lo, int64_t Np, int64_t Rp,
+                             int64_t N, int64_t R);
+cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
+                         cudaStream_t st);
+void tc_force_free(TcForce* tf);
+
+struct TcSyrk;
+cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);
+cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t* err,
+                        cudaStream_t st);
+void tc_syrk_free(TcSyrk* ts);
+
+}  // namespace fth

@@ -1,0 +1,110 @@
+// Device helpers of the GLE step: counter-based noise and the O / B / A updates.
+//
+// Noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor S-box on a 4x32-bit counter with a 2x32-bit key bumped by the Weyl
+// constants between rounds.  For kick index kappa, dof i, replica r, call k uses
+// counter (kappa, i, r, k) and key (seed_lo, seed_hi).  Box-Muller turns each uint32
+// pair (a, b) into two normals rho*cos(2 pi u_b), rho*sin(2 pi u_b) with
+// rho = sqrt(-2 ln u_a) and u(x) = ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and
+// never 0 or 1.  Normals 0..ns-1 drive the O half-step ending step kappa-1, normals
+// ns..2ns-1 the O half-step starting step kappa.
+#pragma once
+
+#include <stdint.h>
+
+#include "fth_internal.h"
+
+namespace fth {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float open_unit(uint32_t x) {
+    return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;  // * 2^-24
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const float rho = sqrtf(-2.0f * logf(open_unit(a)));
+    float sn, cs;
+    sincospif(2.0f * open_unit(b), &sn, &cs);
+    z0 = rho * cs;
+    z1 = rho * sn;
+}
+
+// The 2*NS normals of (kappa, i, r).
+template <int NS>
+__device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t r, uint32_t k0,
+                                            uint32_t k1, float (&xi)[2 * NS]) {
+    constexpr int kCalls = (2 * NS + 3) / 4;
+#pragma unroll
+    for (int k = 0; k < kCalls; ++k) {
+        const uint4 x = philox4x32_10(make_uint4(kappa, i, r, (uint32_t)k), k0, k1);
+        float z[4];
+        box_muller(x.x, x.y, z[0], z[1]);
+        box_muller(x.z, x.w, z[2], z[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * k + j < 2 * NS) xi[4 * k + j] = z[j];
+    }
+}
+
+// Only the normals of one half: first (end of step) or second (start of step).
+template <int NS>
+__device__ __forceinline__ void gle_normals_half(uint32_t kappa, uint32_t i, uint32_t r,
+                                                 uint32_t k0, uint32_t k1, int second,
+                                                 float (&xi)[NS]) {
+    float all[2 * NS];
+    gle_normals<NS>(kappa, i, r, k0, k1, all);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) xi[j] = second ? all[NS + j] : all[j];
+}
+
+// v <- T v + S xi on v = (p, s_1..s_{NS-1}).
+template <int NS, typename Real>
+__device__ __forceinline__ void o_half(Real (&v)[NS], const Real* T, const Real* S,
+                                       const Real* xi) {
+    Real out[NS];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) acc = fma(T[a * kMaxNs + b], v[b], acc);
+#pragma unroll
+        for (int b = 0; b <= a; ++b) acc = fma(S[a * kMaxNs + b], xi[b], acc);
+        out[a] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < NS; ++a) v[a] = out[a];
+}
+
+// One fused launch on one (i, r): mq = (M q)_i at the current positions.
+//   end   : p += -hdt mq;  O(xi[0..NS));  sample
+//   start : O(xi[NS..2NS));  p += -hdt mq;  q += dt p
+template <int NS>
+__device__ __forceinline__ void gle_fused(float& q, float (&v)[NS], float mq, const GleF32& g,
+                                          const float (&xi)[2 * NS], int flags, int observable,
+                                          float& sample) {
+    if (flags & kDoEnd) {
+        v[0] = fmaf(-g.hdt, mq, v[0]);
+        o_half<NS, float>(v, g.T, g.S, xi);
+        sample = observable ? q : v[0];
+    }
+    if (flags & kDoStart) {
+        o_half<NS, float>(v, g.T, g.S, xi + NS);
+        v[0] = fmaf(-g.hdt, mq, v[0]);
+        q = fmaf(g.dt, v[0], q);
+    }
+}
+
+}  // namespace fth

@@ -1,0 +1,204 @@
+// Dense path kernels: FP32 FFMA force GEMM and the element-wise fused GLE step.
+//
+// State planes are [Np][Rp] FP32, replica fastest.  The force kernel writes
+// MQ = M q (the force is -MQ, Eq. 5); the element-wise kernel then applies, per
+// (i, r), the end of the current step (B(dt/2), O(dt/2), sample) and the start of
+// the next one (O(dt/2), B(dt/2), A(dt)) of the GLE velocity Verlet scheme (Eq. 2).
+#include <cuda_bf16.h>
+
+#include "fth_internal.h"
+#include "gle_device.cuh"
+
+namespace fth {
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// -------------------------------------------------------------- element-wise step
+// Thread (i, 4 consecutive replicas); blockDim (32, 8): lanes run along i so the
+// transposed operand stores (q^T[r][i]) are coalesced, and every thread moves one
+// 16-byte vector per plane.
+template <int NS>
+__global__ void __launch_bounds__(256)
+dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
+                 float* __restrict__ q, float* __restrict__ p, float* __restrict__ s,
+                 uint32_t kappa, int flags, int observable, float* __restrict__ ps,
+                 int64_t ps_ld, int64_t slot_off, int op_kind, void* op_hi, void* op_lo,
+                 int Np) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
+    if (i >= N || r0 >= Rp) return;
+    const int64_t plane = (int64_t)Np * Rp;
+    const int64_t off = (int64_t)i * Rp + r0;
+
+    const float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
+    float4 q4 = *reinterpret_cast<const float4*>(q + off);
+    float4 v4[NS];
+    v4[0] = *reinterpret_cast<const float4*>(p + off);
+#pragma unroll
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
+
+    float* qa = reinterpret_cast<float*>(&q4);
+    const float* mqa = reinterpret_cast<const float*>(&mq4);
+    float samp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int r = r0 + e;
+        if (r >= R) continue;
+        float v[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+        float xi[2 * NS];
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r, g.key0, g.key1, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+    }
+    *reinterpret_cast<float4*>(q + off) = q4;
+    *reinterpret_cast<float4*>(p + off) = v4[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
+    if (flags & kDoSample)
+        *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
+            make_float4(samp[0], samp[1], samp[2], samp[3]);
+    if (op_kind == kOpTf32) {
+        float* t = static_cast<float*>(op_hi);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) t[(int64_t)(r0 + e) * Np + i] = to_tf32(qa[e]);
+    } else if (op_kind == kOpBf16x2) {
+        __nv_bfloat16* h = static_cast<__nv_bfloat16*>(op_hi);
+        __nv_bfloat16* l = static_cast<__nv_bfloat16*>(op_lo);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(qa[e]);
+            h[(int64_t)(r0 + e) * Np + i] = hb;
+            l[(int64_t)(r0 + e) * Np + i] = __float2bfloat16_rn(qa[e] - __bfloat162float(hb));
+        }
+    }
+}
+
+cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
+                             const float* MQ, float* q, float* p, float* s, uint32_t kappa,
+                             int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
+                             int op_kind, void* op_hi, void* op_lo, int64_t Np,
+                             cudaStream_t st) {
+    dim3 block(32, 8);
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((Rp / 4 + 7) / 8));
+    const int64_t slot_off = slot * Rp;
+#define FTH_DENSE_CASE(NSV)                                                                  \
+    case NSV:                                                                                \
+        dense_gle_kernel<NSV><<<grid, block, 0, st>>>(g, (int)N, (int)R, (int)Rp, MQ, q, p, s, \
+                                                      kappa, flags, observable, ps, ps_ld,    \
+                                                      slot_off, op_kind, op_hi, op_lo, (int)Np); \
+        break;
+    switch (ns) {
+        FTH_DENSE_CASE(1)
+        FTH_DENSE_CASE(2)
+        FTH_DENSE_CASE(3)
+        FTH_DENSE_CASE(4)
+        FTH_DENSE_CASE(5)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FTH_DENSE_CASE
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- FP32 FFMA force GEMM
+// MQ[i][r] = sum_k M[i][k] q[k][r]; M is [Np][ldm] zero padded (Np multiple of 128),
+// q is [Np][Rp] with zero rows beyond N.  Tile 64 x 64, BK 16, 256 threads, 4 x 4
+// outputs per thread, double-buffered shared memory.
+constexpr int kSgBM = 64, kSgBN = 64, kSgBK = 16;
+
+__global__ void __launch_bounds__(256)
+sgemm_force_kernel(const float* __restrict__ M, int64_t ldm, const float* __restrict__ q,
+                   int Rp, float* __restrict__ MQ, int N, int K) {
+    __shared__ __align__(16) float As[2][kSgBK][kSgBM];
+    __shared__ __align__(16) float Bs[2][kSgBK][kSgBN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int row0 = blockIdx.x * kSgBM, col0 = blockIdx.y * kSgBN;
+    // loader coordinates
+    const int a_row = tid / 4, a_k = (tid % 4) * 4;
+    const int b_k = tid / 16, b_col = (tid % 16) * 4;
+    const bool b_ok = col0 + b_col < Rp;
+
+    float acc[4][4] = {};
+    auto load = [&](int buf, int k0) {
+        const float4 a = *reinterpret_cast<const float4*>(M + (int64_t)(row0 + a_row) * ldm + k0 + a_k);
+        As[buf][a_k + 0][a_row] = a.x;
+        As[buf][a_k + 1][a_row] = a.y;
+        As[buf][a_k + 2][a_row] = a.z;
+        As[buf][a_k + 3][a_row] = a.w;
+        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b_ok) b = *reinterpret_cast<const float4*>(q + (int64_t)(k0 + b_k) * Rp + col0 + b_col);
+        *reinterpret_cast<float4*>(&Bs[buf][b_k][b_col]) = b;
+    };
+    const int nk = K / kSgBK;
+    load(0, 0);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) load(cur ^ 1, (kt + 1) * kSgBK);
+#pragma unroll
+        for (int kk = 0; kk < kSgBK; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+    const int c = col0 + tx * 4;
+    if (c >= Rp) return;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int r = row0 + ty * 4 + x;
+        if (r < N)
+            *reinterpret_cast<float4*>(MQ + (int64_t)r * Rp + c) =
+                make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+    }
+}
+
+cudaError_t launch_sgemm_force(const float* M, int64_t ldm, const float* q, int64_t Rp,
+                               float* MQ, int64_t N, cudaStream_t st) {
+    const int64_t Np = ((N + 127) / 128) * 128;
+    dim3 grid((unsigned)(Np / kSgBM), (unsigned)((Rp + kSgBN - 1) / kSgBN));
+    sgemm_force_kernel<<<grid, 256, 0, st>>>(M, ldm, q, (int)Rp, MQ, (int)N, (int)Np);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- conversions
+__global__ void round_tf32_kernel(float* x, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        x[k] = to_tf32(x[k]);
+}
+
+__global__ void split_bf16_kernel(const float* x, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x[k]);
+        hi[k] = h;
+        lo[k] = __float2bfloat16_rn(x[k] - __bfloat162float(h));
+    }
+}
+
+cudaError_t launch_round_tf32(float* x, int64_t n, cudaStream_t st) {
+    round_tf32_kernel<<<1216, 256, 0, st>>>(x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st) {
+    split_bf16_kernel<<<1216, 256, 0, st>>>(x, n, static_cast<__nv_bfloat16*>(hi),
+                                            static_cast<__nv_bfloat16*>(lo));
+    return cudaGetLastError();
+}
+
+}  // namespace fth

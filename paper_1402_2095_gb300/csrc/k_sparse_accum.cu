@@ -1,0 +1,281 @@
+// Sparse path (fused CSR SpMM + GLE step) and the accumulation kernels.
+//
+// Sparse M (paper, Sec. "The f-thermostat": the force of Eq. 5 is a sparse
+// matrix-vector product, O(N) per step): state planes are [N][Rp] FP32, replica
+// fastest, so the gather of a neighbour row q[col][r..r+3] is one coalesced 16-byte
+// vector per thread and the threads of a row read contiguous memory.
+//
+// Accumulation (Eq. 6 estimator, block averaging of the "2A" accumulators): samples
+// are staged as ps[i][slot * Rp + r]; one pass adds sum_c ps[i][c] ps[j][c] over the
+// staged columns to an FP32 block partial, and a block flush folds partial / (block R)
+// into FP64 Welford (mean, M2) per element.
+#include <algorithm>
+
+#include "fth_internal.h"
+#include "gle_device.cuh"
+
+namespace fth {
+
+// -------------------------------------------------------------- CSR fused step
+// Thread t -> (row i = t / (Rp/4), replicas 4 * (t % (Rp/4)) .. +3).
+template <int NS>
+__global__ void __launch_bounds__(256)
+csr_step_kernel(GleF32 g, int N, int R, int Rp, const int32_t* __restrict__ rowptr,
+                const int32_t* __restrict__ col, const float* __restrict__ val,
+                const float* __restrict__ q_in, float* __restrict__ q_out,
+                float* __restrict__ p, float* __restrict__ s, uint32_t kappa, int flags,
+                int observable, float* __restrict__ ps, int64_t ps_ld, int64_t slot_off) {
+    const int quads = Rp >> 2;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * quads) return;
+    const int i = (int)(t / quads);
+    const int r0 = (int)(t % quads) * 4;
+    const int64_t plane = (int64_t)N * Rp;
+    const int64_t off = (int64_t)i * Rp + r0;
+
+    float4 mq4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e1 = rowptr[i + 1];
+    for (int e = rowptr[i]; e < e1; ++e) {
+        const float m = val[e];
+        const float4 x = *reinterpret_cast<const float4*>(q_in + (int64_t)col[e] * Rp + r0);
+        mq4.x = fmaf(m, x.x, mq4.x);
+        mq4.y = fmaf(m, x.y, mq4.y);
+        mq4.z = fmaf(m, x.z, mq4.z);
+        mq4.w = fmaf(m, x.w, mq4.w);
+    }
+    float4 q4 = *reinterpret_cast<const float4*>(q_in + off);
+    float4 v4[NS];
+    v4[0] = *reinterpret_cast<const float4*>(p + off);
+#pragma unroll
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
+
+    float* qa = reinterpret_cast<float*>(&q4);
+    const float* mqa = reinterpret_cast<const float*>(&mq4);
+    float samp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int r = r0 + e;
+        if (r >= R) continue;
+        float v[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+        float xi[2 * NS];
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r, g.key0, g.key1, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+    }
+    *reinterpret_cast<float4*>(q_out + off) = q4;
+    *reinterpret_cast<float4*>(p + off) = v4[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
+    if (flags & kDoSample)
+        *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
+            make_float4(samp[0], samp[1], samp[2], samp[3]);
+}
+
+cudaError_t launch_csr_step(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
+                            const int32_t* rowptr, const int32_t* col, const float* val,
+                            const float* q_in, float* q_out, float* p, float* s,
+                            uint32_t kappa, int flags, int observable, float* ps,
+                            int64_t ps_ld, int64_t slot, cudaStream_t st) {
+    const int64_t threads = N * (Rp / 4);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const int64_t slot_off = slot * Rp;
+#define FTH_CSR_CASE(NSV)                                                                      \
+    case NSV:                                                                                  \
+        csr_step_kernel<NSV><<<blocks, 256, 0, st>>>(g, (int)N, (int)R, (int)Rp, rowptr, col, val, \
+                                                     q_in, q_out, p, s, kappa, flags,          \
+                                                     observable, ps, ps_ld, slot_off);         \
+        break;
+    switch (ns) {
+        FTH_CSR_CASE(1)
+        FTH_CSR_CASE(2)
+        FTH_CSR_CASE(3)
+        FTH_CSR_CASE(4)
+        FTH_CSR_CASE(5)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FTH_CSR_CASE
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- pair accumulation
+// One warp per tracked pair; ncols and ps_ld are multiples of 4.
+__global__ void __launch_bounds__(256)
+pair_accum_kernel(const float* __restrict__ ps, int64_t ps_ld, int64_t ncols,
+                  const int32_t* __restrict__ pairs, int64_t npairs, float* __restrict__ partial) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= npairs) return;
+    const float* a = ps + (int64_t)pairs[2 * w] * ps_ld;
+    const float* b = ps + (int64_t)pairs[2 * w + 1] * ps_ld;
+    float acc = 0.f;
+    for (int64_t c = lane * 4; c < ncols; c += 128) {
+        const float4 x = *reinterpret_cast<const float4*>(a + c);
+        const float4 y = *reinterpret_cast<const float4*>(b + c);
+        acc = fmaf(x.x, y.x, acc);
+        acc = fmaf(x.y, y.y, acc);
+        acc = fmaf(x.z, y.z, acc);
+        acc = fmaf(x.w, y.w, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) partial[w] += acc;
+}
+
+cudaError_t launch_pair_accum(const float* ps, int64_t ps_ld, int64_t ncols,
+                              const int32_t* pairs, int64_t npairs, float* partial,
+                              cudaStream_t st) {
+    if (npairs <= 0 || ncols <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((npairs * 32 + 255) / 256);
+    pair_accum_kernel<<<blocks, 256, 0, st>>>(ps, ps_ld, ncols, pairs, npairs, partial);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- FP32 FFMA SYRK
+// tiles[t(I,J)][a][b] += sum_c ps[I*128+a][c] ps[J*128+b][c] for the upper tiles I <= J.
+// 256 threads, 8 x 8 outputs each, BK = 8.
+__global__ void __launch_bounds__(256)
+syrk_fp32_kernel(const float* __restrict__ ps, int64_t ps_ld, int64_t ncols, int nbt,
+                 float* __restrict__ tiles) {
+    constexpr int BK = 8;
+    __shared__ __align__(16) float As[BK][kTile];
+    __shared__ __align__(16) float Bs[BK][kTile];
+    int t = blockIdx.x, I = 0;
+    while (t >= nbt - I) {
+        t -= nbt - I;
+        ++I;
+    }
+    const int J = I + t;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const float* A = ps + (int64_t)I * kTile * ps_ld;
+    const float* B = ps + (int64_t)J * kTile * ps_ld;
+    float acc[8][8] = {};
+    const int lr = tid / 2, lk = (tid % 2) * 4;
+    for (int64_t k0 = 0; k0 < ncols; k0 += BK) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (k0 + lk < ncols) {
+            a = *reinterpret_cast<const float4*>(A + (int64_t)lr * ps_ld + k0 + lk);
+            b = *reinterpret_cast<const float4*>(B + (int64_t)lr * ps_ld + k0 + lk);
+        }
+        As[lk + 0][lr] = a.x; As[lk + 1][lr] = a.y; As[lk + 2][lr] = a.z; As[lk + 3][lr] = a.w;
+        Bs[lk + 0][lr] = b.x; Bs[lk + 1][lr] = b.y; Bs[lk + 2][lr] = b.z; Bs[lk + 3][lr] = b.w;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float av[8], bv[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) av[x] = As[kk][ty * 8 + x];
+#pragma unroll
+            for (int y = 0; y < 8; ++y) bv[y] = Bs[kk][tx * 8 + y];
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+    float* out = tiles + (int64_t)blockIdx.x * kTile * kTile;
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) out[(ty * 8 + x) * kTile + tx * 8 + y] += acc[x][y];
+}
+
+cudaError_t launch_syrk_fp32(const float* ps, int64_t ps_ld, int64_t ncols, int64_t Np,
+                             float* tiles, cudaStream_t st) {
+    const int nbt = (int)(Np / kTile);
+    const unsigned ntiles = (unsigned)(nbt * (nbt + 1) / 2);
+    syrk_fp32_kernel<<<ntiles, 256, 0, st>>>(ps, ps_ld, ncols, nbt, tiles);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- block flush
+__global__ void flush_kernel(float* __restrict__ partial, double* __restrict__ mean,
+                             double* __restrict__ m2, int64_t count, double inv_count, double nb,
+                             uint32_t* err) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double b = (double)partial[e] * inv_count;
+        bad |= !isfinite(b);
+        const double d = b - mean[e];
+        const double mu = mean[e] + d / nb;
+        m2[e] += d * (b - mu);
+        mean[e] = mu;
+        partial[e] = 0.f;
+    }
+    if (bad) atomicOr(err, kErrNonFinite);
+}
+
+__global__ void flush64_kernel(double* __restrict__ partial, int64_t R, int64_t stride,
+                               double* __restrict__ mean, double* __restrict__ m2, int64_t count,
+                               double inv_count, double nb, uint32_t* err) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int64_t r = 0; r < R; ++r) {
+            sum += partial[r * stride + e];
+            partial[r * stride + e] = 0.0;
+        }
+        const double b = sum * inv_count;
+        bad |= !isfinite(b);
+        const double d = b - mean[e];
+        const double mu = mean[e] + d / nb;
+        m2[e] += d * (b - mu);
+        mean[e] = mu;
+    }
+    if (bad) atomicOr(err, kErrNonFinite);
+}
+
+cudaError_t launch_flush(float* partial, double* mean, double* m2, int64_t count,
+                         double inv_count, double nb, uint32_t* err, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16);
+    flush_kernel<<<blocks, 256, 0, st>>>(partial, mean, m2, count, inv_count, nb, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flush64(double* partial, int64_t R, int64_t stride, double* mean, double* m2,
+                           int64_t count, double inv_count, double nb, uint32_t* err,
+                           cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16);
+    flush64_kernel<<<blocks, 256, 0, st>>>(partial, R, stride, mean, m2, count, inv_count, nb,
+                                           err);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- gather for fth_elements
+__global__ void gather_kernel(const int64_t* __restrict__ idx, int64_t k,
+                              const double* __restrict__ mean, const double* __restrict__ m2,
+                              const float* __restrict__ partial32,
+                              const double* __restrict__ partial64, int64_t p64_R,
+                              int64_t p64_stride, double* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = idx[e];
+        out[3 * e] = mean[x];
+        out[3 * e + 1] = m2[x];
+        double part = 0.0;
+        if (partial32) part = (double)partial32[x];
+        if (partial64)
+            for (int64_t r = 0; r < p64_R; ++r) part += partial64[r * p64_stride + x];
+        out[3 * e + 2] = part;
+    }
+}
+
+cudaError_t launch_gather(const int64_t* idx, int64_t k, const double* mean, const double* m2,
+                          const float* partial32, const double* partial64, int64_t p64_R,
+                          int64_t p64_stride, double* out, cudaStream_t st) {
+    if (k <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>((k + 255) / 256, 1024);
+    gather_kernel<<<blocks, 256, 0, st>>>(idx, k, mean, m2, partial32, partial64, p64_R,
+                                          p64_stride, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fth

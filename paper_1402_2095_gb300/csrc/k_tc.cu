@@ -1,0 +1,491 @@
+// tcgen05 / TMA kernels for sm_103a: the dense force GEMM (MQ = M q, Eq. 5) and the
+// all-elements accumulator (SYRK of staged samples, Eq. 6 estimator).
+//
+// Both are D[128 x BN] += A[128 x K] B[BN x K]^T with A and B K-major in global
+// memory.  TMA copies 128-byte-wide K slices (SWIZZLE_128B) into a ring of shared
+// memory stages; one thread issues tcgen05.mma (kind::tf32: K = 8 per instruction, or
+// kind::f16 with BF16 operands: K = 16) accumulating in tensor memory (one FP32
+// column per output column, one TMEM lane per output row); tcgen05.commit releases a
+// stage back to the TMA thread and finally signals the epilogue, where each of the 4
+// warps reads its 32 TMEM lanes with tcgen05.ld.
+//
+// Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the thread sets
+// kErrTimeout in the device error word, the roles stop issuing work, outstanding TMA
+// loads are drained with a bounded wait, and the CTA frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "fth_internal.h"
+
+namespace fth {
+namespace {
+
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and the timeout bit set) if the phase did not complete in 1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try(bar, parity)) {
+        if (global_ns() - t0 > kWaitNs) {
+            atomicOr(err, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8 rows x 128 B atoms,
+// atoms 1024 B apart), tcgen05 descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8-row groups
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // swizzle mode: 128B
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = BN.
+// ab_fmt: 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
+__host__ __device__ constexpr uint32_t make_idesc(int ab_fmt, int n) {
+    return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ shared mainloop
+// KIND 1: TF32, one A and one B operand.  KIND 2: split BF16, A = (hi, lo),
+// B = (hi, lo), three products hi*hi + hi*lo + lo*hi per K slice.
+template <int KIND, int BN>
+struct TcCfg {
+    static constexpr int kOps = KIND == 1 ? 1 : 2;               // operand planes
+    static constexpr int kABytes = 128 * 128;                     // one 128-row x 128-B slice
+    static constexpr int kBBytes = BN * 128;
+    static constexpr int kStageBytes = kOps * (kABytes + kBBytes);
+    static constexpr int kKPerSlice = KIND == 1 ? 32 : 64;       // elements per 128 B
+    static constexpr int kKPerMma = KIND == 1 ? 8 : 16;
+    static constexpr int kTmemCols = BN < 32 ? 32 : BN;
+};
+
+struct TcMaps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+template <int KIND, int BN, int STAGES>
+__device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b_row,
+                                            int nslices, uint8_t* stages, uint64_t* full,
+                                            uint64_t* empty, uint64_t* done, uint32_t tmem,
+                                            uint32_t* err) {
+    using C = TcCfg<KIND, BN>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nslices && ok; ++kb) {
+            const int st = kb % STAGES;
+            if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
+            if (!ok) break;
+            uint8_t* base = stages + st * C::kStageBytes;
+            mbar_expect_tx(&full[st], C::kStageBytes);
+            const int x = kb * C::kKPerSlice;
+            tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
+            tma_load_2d(&maps.b_hi, &full[st], base + C::kABytes, x, b_row);
+            if (KIND == 2) {
+                tma_load_2d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, x, a_row);
+                tma_load_2d(&maps.b_lo, &full[st], base + 2 * C::kABytes + C::kBBytes, x, b_row);
+            }
+            ++issued;
+        }
+        if (!ok || *reinterpret_cast<volatile uint32_t*>(err) != 0) {
+            // drain the copies still in flight before the CTA exits (bounded)
+            for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = make_idesc(KIND == 1 ? 2 : 1, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nslices; ++kb) {
+            const int st = kb % STAGES;
+            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err)) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t base = smem_u32(stages + st * C::kStageBytes);
+            const uint64_t ah = sw128_desc(base);
+            const uint64_t bh = sw128_desc(base + C::kABytes);
+#pragma unroll
+            for (int kk = 0; kk < 128 / (C::kKPerMma * (KIND == 1 ? 4 : 2)); ++kk) {
+                const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA K step
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                if (KIND == 1) {
+                    umma<1>(tmem, ah + adv, bh + adv, idesc, acc);
+                } else {
+                    const uint64_t al = sw128_desc(base + C::kABytes + C::kBBytes);
+                    const uint64_t bl = sw128_desc(base + 2 * C::kABytes + C::kBBytes);
+                    umma<2>(tmem, al + adv, bh + adv, idesc, acc);   // lo * hi
+                    umma<2>(tmem, ah + adv, bl + adv, idesc, 1u);    // hi * lo
+                    umma<2>(tmem, ah + adv, bh + adv, idesc, 1u);    // hi * hi
+                }
+            }
+            umma_commit(&empty[st]);
+        }
+        // always signal: the commit also tracks completion of every MMA issued above,
+        // so the epilogue never frees TMEM under an MMA still in flight
+        umma_commit(done);
+        if (!ok) atomicOr(err, kErrTimeout);
+    }
+    __syncwarp();
+}
+
+template <int KIND, int BN, int STAGES>
+__device__ __forceinline__ bool tc_setup(uint8_t*& stages, uint64_t*& full, uint64_t*& empty,
+                                         uint64_t*& done, uint32_t& tmem) {
+    using C = TcCfg<KIND, BN>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    stages = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * C::kStageBytes);
+    full = bars;
+    empty = bars + STAGES;
+    done = bars + 2 * STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(C::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    return true;
+}
+
+template <int KIND, int BN>
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+    using C = TcCfg<KIND, BN>;
+    fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(C::kTmemCols));
+    }
+}
+
+// ------------------------------------------------------------------ force GEMM
+// grid (Np / 128, ceil(Rp / BN)); MQ[row][col] for row < N, col < Rp.
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int ldf, int N,
+                int Rp, int nslices, uint32_t* err) {
+    uint8_t* stages;
+    uint64_t *full, *empty, *done;
+    uint32_t tmem;
+    tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
+    const int row0 = blockIdx.x * 128, col0 = blockIdx.y * BN;
+    tc_mainloop<KIND, BN, STAGES>(maps, row0, col0, nslices, stages, full, empty, done, tmem, err);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    if (ok) {
+        const int row = row0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+            if (row < N) {
+                float* dst = MQ + (int64_t)row * ldf + col0 + c * 16;
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    if (col0 + c * 16 + j + 4 <= Rp)
+                        *reinterpret_cast<float4*>(dst + j) =
+                            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+        }
+    }
+    tc_teardown<KIND, BN>(tmem);
+}
+
+// ------------------------------------------------------------------ SYRK accumulator
+// One CTA per upper tile (I <= J): tiles[t][a][b] += sum_c ps[I*128+a][c] ps[J*128+b][c].
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1)
+tc_syrk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, int nbt,
+               int nslices, uint32_t* err) {
+    uint8_t* stages;
+    uint64_t *full, *empty, *done;
+    uint32_t tmem;
+    tc_setup<1, 128, STAGES>(stages, full, empty, done, tmem);
+    int t = blockIdx.x, I = 0;
+    while (t >= nbt - I) {
+        t -= nbt - I;
+        ++I;
+    }
+    const int J = I + t;
+    tc_mainloop<1, 128, STAGES>(maps, I * 128, J * 128, nslices, stages, full, empty, done, tmem,
+                                err);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    if (ok) {
+        float* out = tiles + (int64_t)blockIdx.x * 128 * 128 + (int64_t)(warp * 32 + lane) * 128;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+            float4* dst = reinterpret_cast<float4*>(out + c * 16);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float4 o = dst[j];
+                o.x += v[4 * j];
+                o.y += v[4 * j + 1];
+                o.z += v[4 * j + 2];
+                o.w += v[4 * j + 3];
+                dst[j] = o;
+            }
+        }
+    }
+    tc_teardown<1, 128>(tmem);
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D K-major map: rows x cols elements, row stride ld elements, box (128 B) x box_rows.
+cudaError_t make_map(CUtensorMap* map, const void* base, int bf16, uint64_t cols, uint64_t rows,
+                     uint64_t ld, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const uint32_t esz = bf16 ? 2 : 4;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * esz};
+    const cuuint32_t box[2] = {128u / esz, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+constexpr int kForceBN = 64;
+constexpr int kForceStages = 6;
+constexpr int kSyrkStages = 4;
+
+template <int KIND, int BN, int STAGES>
+size_t tc_smem_bytes() {
+    return (size_t)STAGES * TcCfg<KIND, BN>::kStageBytes + 1024 + 8 * (2 * STAGES + 2);
+}
+
+}  // namespace
+
+struct TcForce {
+    TcMaps maps;
+    int kind;
+    int64_t Np, Rp, N, R;
+};
+
+struct TcSyrk {
+    TcMaps maps;
+    int64_t Np, ps_ld;
+};
+
+cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const void* A_lo,
+                             const void* B_hi, const void* B_lo, int64_t Np, int64_t Rp,
+                             int64_t N, int64_t R) {
+    TcForce* tf = new TcForce();
+    tf->kind = kind;
+    tf->Np = Np;
+    tf->Rp = Rp;
+    tf->N = N;
+    tf->R = R;
+    const int bf = kind == 2;
+    cudaError_t e = make_map(&tf->maps.a_hi, A_hi, bf, Np, Np, Np, 128);
+    if (e == cudaSuccess) e = make_map(&tf->maps.b_hi, B_hi, bf, Np, Rp, Np, kForceBN);
+    if (e == cudaSuccess && bf) e = make_map(&tf->maps.a_lo, A_lo, bf, Np, Np, Np, 128);
+    if (e == cudaSuccess && bf) e = make_map(&tf->maps.b_lo, B_lo, bf, Np, Rp, Np, kForceBN);
+    if (!bf) {
+        tf->maps.a_lo = tf->maps.a_hi;
+        tf->maps.b_lo = tf->maps.b_hi;
+    }
+    if (e != cudaSuccess) {
+        delete tf;
+        return e;
+    }
+    *out = tf;
+    return cudaSuccess;
+}
+
+cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
+                         cudaStream_t st) {
+    dim3 grid((unsigned)(tf->Np / 128), (unsigned)((tf->Rp + kForceBN - 1) / kForceBN));
+    if (tf->kind == 1) {
+        constexpr int K = 1;
+        const size_t sm = tc_smem_bytes<K, kForceBN, kForceStages>();
+        auto kern = tc_force_kernel<K, kForceBN, kForceStages>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<grid, 128, sm, st>>>(tf->maps, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
+                                    (int)(tf->Np / 32), err);
+    } else {
+        constexpr int K = 2;
+        constexpr int S = 4;
+        const size_t sm = tc_smem_bytes<K, kForceBN, S>();
+        auto kern = tc_force_kernel<K, kForceBN, S>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<grid, 128, sm, st>>>(tf->maps, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
+                                    (int)(tf->Np / 64), err);
+    }
+    return cudaGetLastError();
+}
+
+void tc_force_free(TcForce* tf) { delete tf; }
+
+cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld) {
+    TcSyrk* ts = new TcSyrk();
+    ts->Np = Np;
+    ts->ps_ld = ps_ld;
+    cudaError_t e = make_map(&ts->maps.a_hi, ps, 0, ps_ld, Np, ps_ld, 128);
+    if (e != cudaSuccess) {
+        delete ts;
+        return e;
+    }
+    ts->maps.b_hi = ts->maps.a_hi;
+    ts->maps.a_lo = ts->maps.a_hi;
+    ts->maps.b_lo = ts->maps.a_hi;
+    *out = ts;
+    return cudaSuccess;
+}
+
+cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t* err,
+                        cudaStream_t st) {
+    if (ncols <= 0) return cudaSuccess;
+    const int nbt = (int)(ts->Np / 128);
+    const unsigned ntiles = (unsigned)(nbt * (nbt + 1) / 2);
+    const size_t sm = tc_smem_bytes<1, 128, kSyrkStages>();
+    auto kern = tc_syrk_kernel<kSyrkStages>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int nslices = (int)((ncols + 31) / 32);
+    kern<<<ntiles, 128, sm, st>>>(ts->maps, tiles, nbt, nslices, err);
+    return cudaGetLastError();
+}
+
+void tc_syrk_free(TcSyrk* ts) { delete ts; }
+
+}  // namespace fth

@@ -166,3 +166,14 @@ def test_tau_p2_white_noise():
     ct = np.einsum("j,tj,j->t", V[1, :], np.exp(-np.outer(tt, w)), (Vi @ C)[:, 1]).real
     integral = np.trapezoid(ct ** 2, tt)
     assert np.isclose(gle.tau_p2(lam, a, c), integral / C[1, 1] ** 2, rtol=1e-6)
+
+
+@pytest.mark.parametrize("burnin,n", [(0, 1), (0, 300), (25, 700), (400, 50)])
+def test_transient_mean_closed_form_equals_recursion(burnin, n):
+    a, c = syn.random_gle(4, seed=29, rate=2.0)
+    T, S = gle.propagator(a, c, 0.05)
+    lams = [0.3, 2.0, 35.0]
+    for obs in (0, 1):
+        fast = gle.mode_response_mean(lams, T, S, 0.05, burnin, n, obs)
+        slow = gle.mode_response_mean_recursive(lams, T, S, 0.05, burnin, n, obs)
+        assert np.allclose(fast, slow, rtol=1e-9, atol=1e-12)

@@ -167,3 +167,23 @@ def test_stationary_estimate_within_block_errors():
     assert np.all(np.abs(z) < 4.0), z
     # and not trivially: the estimate moved far from zero
     assert np.all(np.abs(np.diag(ref)) > 10 * errs[[e for e, (i, j) in enumerate(pairs) if i == j]])
+
+
+def test_elementwise_step_equals_c_integrator():
+    n, R = 7, 3
+    M, _, _ = syn.dense_spd(n, 1.0, 30.0, seed=31)
+    a, c = syn.random_gle(4, seed=32, rate=2.0)
+    dt, seed = 0.05, 77
+    o = OracleFTH(M=M, a_p=a, c_p=c, dt=dt, replicas=R, seed=seed)
+    o.run(5)
+    q0, p0, s0 = o.q.copy(), o.p.copy(), o.s.copy()
+    kappa = o.t + 1
+    x = o.run(1, keep_samples=True)[0]
+    from oracle.fth import fused_step_elements
+    elems = [(i, r) for i in range(n) for r in range(R)]
+    qn, pn, sn, xn = fused_step_elements(M, q0, p0, s0, o.T, o.S, dt, seed, kappa, elems)
+    for k, (i, r) in enumerate(elems):
+        assert np.isclose(qn[k], o.q[r, i], rtol=1e-13, atol=1e-14)
+        assert np.isclose(pn[k], o.p[r, i], rtol=1e-13, atol=1e-14)
+        assert np.allclose(sn[k], o.s[r, :, i], rtol=1e-13, atol=1e-14)
+        assert np.isclose(xn[k], x[r, i], rtol=1e-13, atol=1e-14)
