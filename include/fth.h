@@ -105,6 +105,9 @@ typedef struct {
     int64_t npairs;
     int64_t stack;          /* samples staged before one accumulation pass (0 = auto)     */
     void* stream;           /* cudaStream_t                                               */
+    int64_t replica_offset; /* global index of replica 0 in the noise counter: a run split
+                               across processes with offsets 0, R, 2R, ... draws exactly the
+                               noise of one run with all replicas                          */
 } fth_options;
 
 typedef struct {
@@ -162,6 +165,28 @@ void fth_destroy(fth_ctx* ctx);
 /* The library's own O half-step constants in FP64: T = exp(-A_p dt/2) (Pade scaling
  * and squaring) and lower-triangular S with S S^T = C_p - T C_p T^T; (s+1)^2 each. */
 fth_status fth_gle_propagator(const fth_gle* gle, double dt, double* T, double* S);
+
+/* Kernel classes reported by fth_profile_read. */
+enum fth_kernel_class {
+    FTH_K_FORCE_FP32 = 0,   /* FFMA force GEMM                                  */
+    FTH_K_FORCE_TC = 1,     /* tcgen05 force GEMM (TF32 or split BF16)          */
+    FTH_K_GLE_DENSE = 2,    /* element-wise fused GLE step, dense path           */
+    FTH_K_CSR_STEP = 3,     /* fused CSR SpMM + GLE step                         */
+    FTH_K_PAIR_ACCUM = 4,   /* pair-list accumulation pass                       */
+    FTH_K_SYRK_FP32 = 5,    /* FFMA all-elements accumulation pass               */
+    FTH_K_SYRK_TC = 6,      /* tcgen05 all-elements accumulation pass            */
+    FTH_K_FLUSH = 7,        /* FP64 block flush                                  */
+    FTH_K_FP64_DENSE = 8,   /* FP64 one-CTA-per-replica segment                  */
+    FTH_K_CLASSES = 9
+};
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel the context launches:
+ * one event pair around each launch on the context's stream (off by default). */
+fth_status fth_profile_enable(fth_ctx* ctx, int enable);
+
+/* Synchronise, then return per kernel class the summed device milliseconds and the
+ * launch counts recorded since the last read (arrays of FTH_K_CLASSES entries). */
+fth_status fth_profile_read(fth_ctx* ctx, double* ms, int64_t* launches);
 
 /* Library version string. */
 const char* fth_version(void);

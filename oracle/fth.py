@@ -19,7 +19,8 @@ from . import gle, native
 
 class OracleFTH:
     def __init__(self, M=None, csr=None, a_p=None, c_p=None, dt=0.01, replicas=1, seed=0,
-                 burnin=0, block=1, observable=0, pairs=None, T=None, S=None):
+                 burnin=0, block=1, observable=0, pairs=None, T=None, S=None,
+                 replica_offset=0):
         if (M is None) == (csr is None):
             raise ValueError("give exactly one of M (dense) or csr=(rowptr, col, val, n)")
         if M is not None:
@@ -46,6 +47,7 @@ class OracleFTH:
         self.burnin = int(burnin)
         self.block = int(block)
         self.observable = int(observable)
+        self.roff = int(replica_offset)
         n, R, ns = self.n, self.R, self.ns
         self.q = np.zeros((R, n))
         self.p = np.zeros((R, n))
@@ -71,7 +73,7 @@ class OracleFTH:
         P = native.ptr
         return (native.I64(self.n), native.I64(self.R), native.INT(self.ns), native.INT(self.kind),
                 P(self.Md), P(self.rowptr), P(self.col), P(self.val), P(self.T), P(self.S),
-                native.D(self.dt), native.U64(self.seed))
+                native.D(self.dt), native.U64(self.seed), native.U32(self.roff))
 
     def run(self, steps: int, keep_samples: bool = False):
         L = native.lib()

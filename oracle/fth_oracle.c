@@ -23,7 +23,8 @@
  *   u(x) = ((x >> 9) * 2 + 1) * 2^-24,  rho = sqrt(-2 ln u(x0)),
  *   n0 = rho cos(2 pi u(x1)),  n1 = rho sin(2 pi u(x1)).
  * Normals 0..ns-1 of kappa drive the O half-step that ends step kappa-1,
- * normals ns..2ns-1 drive the O half-step that starts step kappa.
+ * normals ns..2ns-1 drive the O half-step that starts step kappa.  The replica
+ * index in the counter is r + roff (roff: global index of the first replica).
  *
  * State layout: q[R][n], p[R][n], s[R][ns-1][n]  (replica-major).
  */
@@ -138,7 +139,7 @@ static void store_v(int64_t n, int ns, int64_t r, int64_t i, double* p, double* 
 int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
                     const int64_t* rowptr, const int64_t* col, const double* val,
                     const double* T, const double* S, double dt, uint64_t seed,
-                    uint32_t kappa, double* q, double* p, double* s)
+                    uint32_t roff, uint32_t kappa, double* q, double* p, double* s)
 {
     if (ns < 1 || ns > NS_MAX) return -1;
     double* F = (double*)malloc(sizeof(double) * (size_t)(n * R));
@@ -148,7 +149,7 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
     for (int64_t r = 0; r < R; ++r) {
         double xi[2 * NS_MAX], v[NS_MAX];
         for (int64_t i = 0; i < n; ++i) {
-            oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r, 2 * ns, xi);
+            oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, 2 * ns, xi);
             load_v(n, ns, r, i, p, s, v);
             o_half(ns, T, S, v, xi + ns);
             v[0] += 0.5 * dt * F[r * n + i];
@@ -177,7 +178,7 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
 int oracle_steps(int64_t n, int64_t R, int ns, int kind, const double* Md,
                  const int64_t* rowptr, const int64_t* col, const double* val,
                  const double* T, const double* S, double dt, uint64_t seed,
-                 uint32_t kappa0, int64_t nsteps, double* q, double* p, double* s,
+                 uint32_t roff, uint32_t kappa0, int64_t nsteps, double* q, double* p, double* s,
                  int observable, double* samples,
                  int64_t npairs, const int64_t* pairs, int64_t burnin, int64_t block,
                  int64_t* nsamp, double* partial, int64_t* inblock,
@@ -199,7 +200,7 @@ int oracle_steps(int64_t n, int64_t R, int ns, int kind, const double* Md,
             double xi[2 * NS_MAX], v[NS_MAX];
             for (int64_t i = 0; i < n; ++i) {
                 const double f = F[r * n + i];
-                oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r, 2 * ns, xi);
+                oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, 2 * ns, xi);
                 load_v(n, ns, r, i, p, s, v);
                 v[0] += 0.5 * dt * f;          /* B(dt/2), end of the current step */
                 o_half(ns, T, S, v, xi);       /* O(dt/2), end of the current step */

@@ -28,7 +28,9 @@ PLANE = {"q": 0, "p": 1, "s": 2}
 # Every symbol include/fth.h declares.
 EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_get_state",
            "fth_set_state", "fth_info", "fth_status_poll", "fth_last_error", "fth_destroy",
-           "fth_gle_propagator", "fth_version")
+           "fth_gle_propagator", "fth_version", "fth_profile_enable", "fth_profile_read")
+KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
+                  "syrk_tc", "flush", "fp64_dense")
 
 
 class FthError(RuntimeError):
@@ -51,7 +53,8 @@ class fth_options(ctypes.Structure):
     _fields_ = [("replicas", ctypes.c_int64), ("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
                 ("burnin", ctypes.c_int64), ("block", ctypes.c_int64), ("observable", ctypes.c_int),
                 ("precision", ctypes.c_int), ("track", ctypes.c_int), ("pairs", ctypes.c_void_p),
-                ("npairs", ctypes.c_int64), ("stack", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("npairs", ctypes.c_int64), ("stack", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("replica_offset", ctypes.c_int64)]
 
 
 class fth_info_t(ctypes.Structure):
@@ -88,6 +91,8 @@ def load(path: str = LIB_PATH):
         "fth_destroy": ([P], None),
         "fth_gle_propagator": ([P, D, P, P], INT),
         "fth_version": ([], ctypes.c_char_p),
+        "fth_profile_enable": ([P, INT], INT),
+        "fth_profile_read": ([P, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -135,7 +140,7 @@ class FTH:
 
     def __init__(self, M=None, csr=None, *, a_p, c_p, dt, replicas, seed=0, burnin=0,
                  block=1000, observable="p", precision="fp32", track="list", pairs=None,
-                 stack=0, stream=None):
+                 stack=0, stream=None, replica_offset=0):
         import torch
 
         L = load()
@@ -198,6 +203,7 @@ class FTH:
             opt.pairs = pr.ctypes.data
             opt.npairs = pr.shape[0]
         opt.stack = int(stack)
+        opt.replica_offset = int(replica_offset)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opt.stream = self.stream.cuda_stream
         nbytes = ctypes.c_size_t(0)
@@ -244,6 +250,18 @@ class FTH:
         i = fth_info_t()
         _check(load().fth_info(self.ctx, ctypes.byref(i)), self.ctx)
         return {f: getattr(i, f) for f, _ in fth_info_t._fields_}
+
+    def profile(self, enable: bool = True):
+        """Turn per-launch CUDA-event timing on or off."""
+        _check(load().fth_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
+
+    def profile_read(self) -> dict:
+        """{kernel class: (total device ms, launches)} since the last read."""
+        n = len(KERNEL_CLASSES)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        _check(load().fth_profile_read(self.ctx, ms.ctypes.data, cnt.ctypes.data), self.ctx)
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES) if cnt[i]}
 
     def poll(self):
         _check(load().fth_status_poll(self.ctx), self.ctx)

@@ -181,6 +181,8 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
     if (o->track == FTH_TRACK_LIST && (o->npairs < 0 || (o->npairs > 0 && !o->pairs)))
         return fail(msg, FTH_E_INVALID_ARG, "pairs");
     if (o->stack < 0) return fail(msg, FTH_E_INVALID_ARG, "stack must be >= 0");
+    if (o->replica_offset < 0 || o->replica_offset + o->replicas > (1ll << 32))
+        return fail(msg, FTH_E_INVALID_ARG, "replica_offset + replicas must fit in 32 bits");
 
     *L = Layout();
     L->ns = gle->s + 1;
@@ -347,6 +349,16 @@ struct fth_ctx {
     int64_t t = 0, nsamp = 0, accumulated = 0, inblock = 0, nfill = 0, nblocks = 0, launches = 0;
     int primed = 0, cur = 0;
     std::string last_error;
+    // opt-in per-launch event timing
+    bool prof = false;
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[FTH_K_CLASSES] = {};
+    int64_t prof_n[FTH_K_CLASSES] = {};
 };
 
 namespace {
@@ -369,6 +381,32 @@ fth_status cuda_fail(fth_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
+cudaEvent_t prof_event(fth_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with an event pair when profiling is on.
+struct ProfScope {
+    fth_ctx* c;
+    bool on;
+    ProfScope(fth_ctx* ctx, int cls) : c(ctx), on(ctx->prof) {
+        if (!on) return;
+        fth_ctx::ProfRec r{cls, prof_event(c), prof_event(c)};
+        cudaEventRecord(r.a, c->stream);
+        c->prof_recs.push_back(r);
+    }
+    ~ProfScope() {
+        if (on) cudaEventRecord(c->prof_recs.back().b, c->stream);
+    }
+};
+
 bool is_tc(const fth_ctx* c) {
     return c->L.path == kPathDense32 &&
            (c->L.precision == FTH_PREC_TF32 || c->L.precision == FTH_PREC_BF16X3);
@@ -376,6 +414,7 @@ bool is_tc(const fth_ctx* c) {
 
 fth_status force(fth_ctx* c) {
     const Layout& L = c->L;
+    ProfScope ps(c, is_tc(c) ? FTH_K_FORCE_TC : FTH_K_FORCE_FP32);
     if (is_tc(c)) {
         FTH_CK(tc_force_run(c->tcf, c->MQ, L.Rp, c->err, c->stream), "tc force");
     } else {
@@ -391,6 +430,8 @@ fth_status accumulate(fth_ctx* c) {
     const Layout& L = c->L;
     if (c->nfill == 0) return FTH_OK;
     const int64_t ncols = c->nfill * L.Rp;
+    ProfScope ps(c, L.track == FTH_TRACK_ALL ? (is_tc(c) ? FTH_K_SYRK_TC : FTH_K_SYRK_FP32)
+                                             : FTH_K_PAIR_ACCUM);
     if (L.track == FTH_TRACK_ALL) {
         if (is_tc(c)) {
             FTH_CK(tc_syrk_run(c->tcs, ncols, static_cast<float*>(c->partial), c->err, c->stream),
@@ -414,6 +455,7 @@ fth_status flush(fth_ctx* c) {
     const Layout& L = c->L;
     const double inv = 1.0 / ((double)c->block * (double)L.R);
     const double nb = (double)(c->nblocks + 1);
+    ProfScope ps(c, FTH_K_FLUSH);
     if (L.path == kPathDense64) {
         FTH_CK(launch_flush64(static_cast<double*>(c->partial), L.R, L.count, c->mean, c->m2,
                               L.count, inv, nb, c->err, c->stream),
@@ -450,6 +492,7 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
     if (!c->primed) {
         fth_status st = force(c);
         if (st != FTH_OK) return st;
+        ProfScope ps(c, FTH_K_GLE_DENSE);
         FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s, (uint32_t)c->t,
                                 kDoStart, c->observable, c->ps, L.ps_ld, 0, opk, hi, lo, L.Np,
                                 c->stream),
@@ -462,10 +505,13 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
         if (st != FTH_OK) return st;
         const bool take = c->nsamp >= c->burnin;
         const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0);
+        {
+        ProfScope ps(c, FTH_K_GLE_DENSE);
         FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s,
                                 (uint32_t)(c->t + 1), flags, c->observable, c->ps, L.ps_ld,
                                 c->nfill, opk, hi, lo, L.Np, c->stream),
                "gle step");
+        }
         ++c->launches;
         ++c->t;
         ++c->nsamp;
@@ -493,6 +539,7 @@ fth_status run_csr(fth_ctx* c, int64_t steps) {
     auto launch = [&](int flags, uint32_t kappa) -> fth_status {
         float* qin = static_cast<float*>(c->q[c->cur]);
         float* qout = static_cast<float*>(c->q[c->cur ^ 1]);
+        ProfScope ps(c, FTH_K_CSR_STEP);
         FTH_CK(launch_csr_step(L.ns, c->g32, L.N, L.R, L.Rp, c->rowptr, c->col, c->val, qin, qout,
                                p, s, kappa, flags, c->observable, c->ps, L.ps_ld, c->nfill,
                                c->stream),
@@ -543,12 +590,15 @@ fth_status run_dense64(fth_ctx* c, int64_t steps) {
         }
         seg = std::min<int64_t>(seg, 1 << 20);
         const uint32_t kappa0 = (uint32_t)(c->primed ? c->t + 1 : c->t);
+        {
+        ProfScope ps(c, FTH_K_FP64_DENSE);
         FTH_CK(launch_fp64_dense(L.ns, c->g64, L.N, L.Np, L.R, static_cast<const double*>(c->M),
                                  static_cast<double*>(c->q[0]), static_cast<double*>(c->p),
                                  static_cast<double*>(c->s), kappa0, seg, c->primed,
                                  c->observable, c->pairs, L.ntracked,
                                  static_cast<double*>(c->partial), acc_from, c->stream),
                "fp64 dense");
+        }
         ++c->launches;
         c->primed = 1;
         c->t += seg;
@@ -655,9 +705,10 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     const int ns = L.ns;
     for (int a = 0; a < ns; ++a)
         for (int b = 0; b < ns; ++b) {
-            c->g32.T[a * kMaxNs + b] = (float)c->T[a * ns + b];
+            const double d = c->T[a * ns + b] - (a == b ? 1.0 : 0.0);   // D = T - I
+            c->g32.T[a * kMaxNs + b] = (float)d;
             c->g32.S[a * kMaxNs + b] = (float)c->S[a * ns + b];
-            c->g64.T[a * kMaxNs + b] = c->T[a * ns + b];
+            c->g64.T[a * kMaxNs + b] = d;
             c->g64.S[a * kMaxNs + b] = c->S[a * ns + b];
         }
     c->g32.dt = (float)opt->dt;
@@ -666,6 +717,7 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     c->g64.hdt = 0.5 * opt->dt;
     c->g32.key0 = c->g64.key0 = (uint32_t)opt->seed;
     c->g32.key1 = c->g64.key1 = (uint32_t)(opt->seed >> 32);
+    c->g32.roff = c->g64.roff = (uint32_t)opt->replica_offset;
 
     auto at = [&](size_t off) { return static_cast<void*>(c->ws + off); };
     c->M = at(L.off_M);
@@ -1027,8 +1079,41 @@ fth_status fth_info(const fth_ctx* c, fth_info_t* info) {
     return FTH_OK;
 }
 
+fth_status fth_profile_enable(fth_ctx* c, int enable) {
+    if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
+    c->prof = enable != 0;
+    return FTH_OK;
+}
+
+fth_status fth_profile_read(fth_ctx* c, double* ms, int64_t* launches) {
+    if (!c || !ms || !launches) return fail(nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    for (auto& r : c->prof_recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.cls] += t;
+            c->prof_n[r.cls] += 1;
+        }
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+    for (int k = 0; k < FTH_K_CLASSES; ++k) {
+        ms[k] = c->prof_ms[k];
+        launches[k] = c->prof_n[k];
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    return FTH_OK;
+}
+
 void fth_destroy(fth_ctx* c) {
     if (!c) return;
+    for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof_pool) cudaEventDestroy(e);
     if (c->tcf) tc_force_free(c->tcf);
     if (c->tcs) tc_syrk_free(c->tcs);
     delete c;

@@ -12,11 +12,13 @@ constexpr int kMaxNs = 5;          // s + 1 <= 5 (s <= 4 auxiliary momenta)
 constexpr int kTile = 128;         // tcgen05 M tile (rows per CTA) and SYRK tile edge
 
 // O half-step constants in FP32 (the FP64 originals are built on the host).
+// T holds D = T - I (the increment form used by the O half-step), S is lower triangular.
 struct GleF32 {
     float T[kMaxNs * kMaxNs];
-    float S[kMaxNs * kMaxNs];   // lower triangular
+    float S[kMaxNs * kMaxNs];
     float dt, hdt;
     uint32_t key0, key1;
+    uint32_t roff;   // replica offset in the noise counter
 };
 
 struct GleF64 {
@@ -24,6 +26,7 @@ struct GleF64 {
     double S[kMaxNs * kMaxNs];
     double dt, hdt;
     uint32_t key0, key1;
+    uint32_t roff;
 };
 
 // Bits of the device error word.

@@ -70,19 +70,21 @@ __device__ __forceinline__ void gle_normals_half(uint32_t kappa, uint32_t i, uin
     for (int j = 0; j < NS; ++j) xi[j] = second ? all[NS + j] : all[j];
 }
 
-// v <- T v + S xi on v = (p, s_1..s_{NS-1}).
+// v <- T v + S xi on v = (p, s_1..s_{NS-1}), with T passed as D = T - I: the
+// increment D v + S xi is formed first and added to v once, so rounding D (whose
+// entries are O(dt |A_p|)) costs far less than rounding T itself would.
 template <int NS, typename Real>
-__device__ __forceinline__ void o_half(Real (&v)[NS], const Real* T, const Real* S,
+__device__ __forceinline__ void o_half(Real (&v)[NS], const Real* D, const Real* S,
                                        const Real* xi) {
     Real out[NS];
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
         Real acc = Real(0);
 #pragma unroll
-        for (int b = 0; b < NS; ++b) acc = fma(T[a * kMaxNs + b], v[b], acc);
+        for (int b = 0; b < NS; ++b) acc = fma(D[a * kMaxNs + b], v[b], acc);
 #pragma unroll
         for (int b = 0; b <= a; ++b) acc = fma(S[a * kMaxNs + b], xi[b], acc);
-        out[a] = acc;
+        out[a] = v[a] + acc;
     }
 #pragma unroll
     for (int a = 0; a < NS; ++a) v[a] = out[a];

@@ -52,7 +52,7 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[2 * NS];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r, g.key0, g.key1, xi);
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.key0, g.key1, xi);
         gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];

@@ -73,7 +73,7 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         __syncthreads();   // all reads of qs done before it is overwritten
         if (i < N) {
             double xi[2 * NS];
-            gle_normals64<NS>(kappa, (uint32_t)i, (uint32_t)r, g.key0, g.key1, xi);
+            gle_normals64<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.key0, g.key1, xi);
             if (!pro) {
                 v[0] = fma(-g.hdt, mq, v[0]);
                 o_half<NS, double>(v, g.T, g.S, xi);
