@@ -188,6 +188,34 @@ fth_status fth_profile_enable(fth_ctx* ctx, int enable);
  * launch counts recorded since the last read (arrays of FTH_K_CLASSES entries). */
 fth_status fth_profile_read(fth_ctx* ctx, double* ms, int64_t* launches);
 
+/* One dense FP32 fused launch that allocates nothing, for callers that cannot allocate
+ * device memory: a plugin whose host framework owns all device memory through its own
+ * pool, a real-time loop that must never enter an allocator, or code that can only pass
+ * pointers it already owns.  No workspace is taken; the intermediate force M q lives in
+ * a library-owned static device array of 4,194,304 floats (16 MiB) per device, kept
+ * until the process exits.  The paper has no counterpart: this is only an allocation
+ * policy of the library.
+ *
+ * Computes, on device buffers the caller owns (all FP32, 16-byte aligned):
+ *   mode 0: MQ = M q; end of the current step (B, O, sample) and start of the next
+ *           (O, B, A) with kick index kappa, exactly as one step of fth_run;
+ *   mode 1: MQ = M q; only the start half (the prologue of a fresh run).
+ * M: [n][ldm] row-major.  q, p: [n][ldr], replica fastest, ldr >= replicas, ldr % 4 == 0.
+ * s: s_aux planes of [n][ldr], contiguous.  sample (mode 0, may be NULL): [n][ldr] gets p
+ * at the end of the step.  T, S: (s_aux+1)^2 FP64 from fth_gle_propagator.  Noise is the
+ * same Philox stream as fth_run with the same seed (replica offset 0).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture.  Every
+ * call shares the one array and leaves its last contents there; each call overwrites
+ * every entry it reads, so nothing needs clearing.  Calls that overlap on the GPU (two
+ * streams, or two host threads on one device) race on the array: serialise them.
+ * Errors: INVALID_ARG (pointers, sizes, alignment), UNSUPPORTED when n * ldr exceeds the
+ * array (4,194,304 floats), CUDA. */
+fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t ldm, float* q, float* p,
+                                  float* s, int64_t replicas, int64_t ldr, int s_aux,
+                                  const double* T, const double* S, double dt, uint64_t seed,
+                                  uint32_t kappa, int mode, float* sample, void* stream);
+
 /* Library version string. */
 const char* fth_version(void);
 

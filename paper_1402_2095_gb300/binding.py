@@ -28,7 +28,8 @@ PLANE = {"q": 0, "p": 1, "s": 2}
 # Every symbol include/fth.h declares.
 EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_get_state",
            "fth_set_state", "fth_info", "fth_status_poll", "fth_last_error", "fth_destroy",
-           "fth_gle_propagator", "fth_version", "fth_profile_enable", "fth_profile_read")
+           "fth_gle_propagator", "fth_version", "fth_profile_enable", "fth_profile_read",
+           "fth_dense_step_noalloc")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense")
 
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH):
         "fth_version": ([], ctypes.c_char_p),
         "fth_profile_enable": ([P, INT], INT),
         "fth_profile_read": ([P, P, P], INT),
+        "fth_dense_step_noalloc": ([P, I64, I64, P, P, P, I64, I64, INT, P, P, D,
+                                    ctypes.c_uint64, ctypes.c_uint32, INT, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
