@@ -27,6 +27,7 @@ def _problem():
 
 def _rank(rank, world, port, R, steps, q):
     os.environ["OMP_NUM_THREADS"] = "1"   # tiny problem: no OpenMP team per rank
+    os.environ["GLOO_SOCKET_IFNAME"] = "lo"   # loopback: no hostname lookup
     import torch.distributed as dist
     from oracle.fth import OracleFTH
     from paper_1402_2095_gb300.multi import combine
@@ -50,8 +51,16 @@ def test_two_rank_combine_equals_single_run():
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_rank, args=(r, world, port, R, steps, q)) for r in range(world)]
-    for p in procs:
-        p.start()
+    saved = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"      # children inherit it before any runtime starts
+    try:
+        for p in procs:
+            p.start()
+    finally:
+        if saved is None:
+            os.environ.pop("OMP_NUM_THREADS")
+        else:
+            os.environ["OMP_NUM_THREADS"] = saved
     cv, ce = q.get(timeout=300)
     for p in procs:
         p.join(timeout=300)
