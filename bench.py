@@ -1,15 +1,21 @@
 #!/usr/bin/env python3
 """Throughput of the f-thermostat hot path on GB300: GLE replica-steps per second.
 
-Workload (one GPU): dense SPD M, N = 4096, M = Q diag(lam) Q^T with Q Haar and lam
-log-uniform in [1, 1e3] (seeded), f = Fermi(beta = 5, mu = median lam), GLE with s = 4
-fitted on the host, dt = 0.1 / sqrt(1e3), R = 256 replicas, FP32 state, force GEMM in
-the chosen precision, every element of <p p^T> accumulated (FP32 block partials, FP64
-block sums).  One step = force, B, O, sample + accumulate, O, B, A over all replicas.
+Default workload (one GPU): dense SPD M, N = 4096, M = Q diag(lam) Q^T with Q Haar and
+lam log-uniform in [1, 1e3] (seeded), f = Fermi(beta = 5, mu = median lam), GLE with
+s = 4 fitted on the host, dt = 0.1 / sqrt(1e3), R = 256 replicas, FP32 state, force
+GEMM in the chosen precision (TF32 by default), every element of <p p^T> accumulated
+(FP32 block partials, FP64 block sums).  One step = force, B, O, sample + accumulate,
+O, B, A over all replicas.
+
+Other workloads (--workload): small_fp64 (N = 32 dense FP64, R = 16, all elements) and
+lattice64 (64^3 periodic lattice, CSR FP32, R = 64, diagonal + nearest-neighbour
+elements).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own replicas of the
-same matrix (replicas are independent: weak scaling, no collective in the timed region).
+                       [--workload dense4096|small_fp64|lattice64] [--precision ...]
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own slice of replicas
+(replica_offset = rank * R, same seed): weak scaling, no collective in the timed region.
 """
 from __future__ import annotations
 
@@ -30,33 +36,114 @@ if ROOT not in sys.path:
 
 import fth_synth as syn  # noqa: E402
 
-N, LAM, R, BETA = 4096, (1.0, 1000.0), 256, 5.0
-SEED = syn.BASE_SEED + 1
-BLOCK = 1000
 METRIC, UNIT = "GLE replica-steps/s", "replica-steps/s"
-WORKLOAD = "dense SPD N=4096, lambda log-uniform [1,1e3], Fermi beta=5 mu=median, R=256, all elements"
-L2_BYTES = 129 * 2 ** 20
-CPU_SAMPLE_REPLICAS = 16
 CPU_BUDGET_S = 15.0
 REF_BUDGET_S = 90.0
+
+
+# ---------------------------------------------------------------------- workloads
+class Workload:
+    """One synthetic problem: matrix, GLE, context options and the algorithmic work of
+    each kernel class per launch (for the roofline)."""
+
+    def __init__(self, name, precision):
+        self.name = name
+        from paper_1402_2095_gb300 import fit
+        self.M32 = self.M64 = self.csr = None
+        self.nnz = 0
+        if name == "dense4096":
+            self.n, self.R, self.block = 4096, 256, 1000
+            self.seed = syn.BASE_SEED + 1
+            M, lam, _ = syn.dense_spd(self.n, 1.0, 1000.0, seed=self.seed)
+            self.mu = float(np.median(lam))
+            self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("fermi_b5_1_1000")
+            self.M32 = M.astype(np.float32)
+            self.precision = precision
+            self.track, self.pairs = "all", None
+            self.label = ("dense SPD N=4096, lambda log-uniform [1,1e3], Fermi beta=5 mu=median, "
+                          "R=256, all elements")
+            self.default_steps, self.cpu_replicas = 20000, 16
+        elif name == "small_fp64":
+            self.n, self.R, self.block = 32, 16, 1000
+            self.seed = syn.BASE_SEED + 0
+            M, lam, _ = syn.dense_spd(self.n, 1.0, 100.0, seed=self.seed)
+            self.mu = None
+            self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("inv_sqrt_1_100")
+            self.M64 = M
+            self.precision = "fp64"
+            self.track, self.pairs = "all", None
+            self.label = ("dense SPD N=32 FP64, lambda log-uniform [1,100], f=x^-1/2, R=16, "
+                          "all 528 elements")
+            self.default_steps, self.cpu_replicas = 100000, 16
+        elif name == "lattice64":
+            L = 64
+            self.n, self.R, self.block = L ** 3, 64, 1000
+            self.seed = syn.BASE_SEED + 2
+            rowptr, col, val = syn.lattice_csr(L, seed=self.seed)
+            self.csr = (rowptr, col, val.astype(np.float32), self.n)
+            self.nnz = len(col)
+            self.mu = 7.0
+            self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("fermi_b2_lattice")
+            self.precision = "fp32"
+            self.track = "list"
+            self.pairs = np.concatenate([syn.diag_pairs(self.n), syn.lattice_nn_pairs(L)])
+            self.label = ("64^3 periodic lattice CSR (N=262144, 7-point), Fermi beta=2 mu=7, "
+                          "R=64, diagonal + nearest-neighbour elements")
+            self.default_steps, self.cpu_replicas = 2000, 4
+        else:
+            raise ValueError(name)
+
+    def matrix_kwargs(self, device, pinned=False):
+        import torch
+        if self.csr is not None:
+            return {"csr": self.csr}
+        if self.precision == "fp64":
+            return {"M": self.M64}
+        t = torch.from_numpy(self.M32)
+        if device:
+            return {"M": t.cuda()}
+        return {"M": t.pin_memory() if pinned else t}
+
+    def element_pairs(self):
+        if self.pairs is not None:
+            return self.pairs
+        return syn.upper_pairs(self.n)
+
+    def oracle_matrix(self):
+        if self.csr is not None:
+            rowptr, col, val, n = self.csr
+            return {"csr": (rowptr, col, val.astype(np.float64), n)}
+        M = self.M64 if self.precision == "fp64" else self.M32.astype(np.float64)
+        return {"M": M}
+
+    def work(self, cls, info):
+        """(bound, algorithmic amount per launch) of a kernel class."""
+        n, R = self.n, self.R
+        if cls in ("force_tc", "force_fp32"):
+            return ("tensor" if cls == "force_tc" else "alu", 2.0 * n * n * R)
+        if cls in ("syrk_tc", "syrk_fp32"):
+            return ("tensor" if cls == "syrk_tc" else "alu", float(n) * (n + 1) * info["stack_cols"])
+        if cls == "gle_dense":
+            op = 4 if self.precision in ("tf32", "bf16x3") else 0
+            return ("hbm", float(28 + 24 + 4 + op) * n * R)
+        if cls == "csr_step":
+            return ("hbm", float(24 + 24 + 4) * n * R + 8.0 * self.nnz + 4.0 * n)
+        if cls == "pair_accum":
+            return ("hbm", 2.0 * 4 * info["stack_cols"] * len(self.element_pairs()))
+        if cls == "fp64_dense":
+            ns = 5
+            per = 2.0 * n * n + 2 * 2 * (ns * ns + ns * (ns + 1) / 2) * n + 2.0 * n * (n + 1) / 2
+            return ("fp64", info["steps_per_launch"] * R * per)
+        return ("hbm", float("nan"))
 
 
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            d = json.load(fh)
-        return d, "measured"
+            return json.load(fh), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
-
-
-def _workload():
-    M, lam, _ = syn.dense_spd(N, LAM[0], LAM[1], seed=SEED)
-    mu = float(np.median(lam))
-    from paper_1402_2095_gb300 import fit
-    a_p, c_p, dt, rep = fit.load_gle("fermi_b5_1_1000")
-    return M, lam, mu, a_p, c_p, dt, rep
 
 
 # ---------------------------------------------------------------------- clocks
@@ -125,57 +212,61 @@ def _traffic(kernel):
     return None
 
 
-def roofline(prof, precision, n, R, stack_cols, peaks, peak_kind):
-    """Dominant kernel (largest device time) against its bound."""
+def roofline(prof, wl, info, peaks, peak_kind):
+    """Dominant kernel (largest total device time) against its bound."""
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     per_launch_s = ms / cnt / 1e3
+    bound, amount = wl.work(name, info)
     tf32_ratio = 1.1 / 2.25           # nominal dense TF32 / BF16 tensor rate
     sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     fp32_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    if name == "force_tc":
-        flops = 2.0 * n * n * R
-        peak = sustained * (tf32_ratio if precision == "tf32" else 1.0)
-        out = {"bound": "tensor", "unit": "TFLOP/s", "achieved": flops / per_launch_s / 1e12,
-               "peak": peak}
-    elif name == "syrk_tc":
-        flops = float(n) * (n + 1) * stack_cols
-        out = {"bound": "tensor", "unit": "TFLOP/s", "achieved": flops / per_launch_s / 1e12,
-               "peak": sustained * tf32_ratio}
-    elif name in ("force_fp32", "syrk_fp32"):
-        flops = 2.0 * n * n * R if name == "force_fp32" else float(n) * (n + 1) * stack_cols
-        out = {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / per_launch_s / 1e12,
-               "peak": fp32_alu}
-    else:   # gle_dense: HBM bytes per element (see DESIGN.md)
-        op_bytes = {"tf32": 4, "bf16x3": 4, "fp32": 0}[precision]
-        byts = (28 + 24 + 4 + op_bytes) * n * R
-        out = {"bound": "hbm", "unit": "GB/s", "achieved": byts / per_launch_s / 1e9,
-               "peak": peaks["hbm_gbs"]}
+    if bound == "tensor":
+        tf = wl.precision == "tf32" or name == "syrk_tc"
+        peak = sustained * (tf32_ratio if tf else 1.0)
+        out = {"bound": "tensor", "unit": "TFLOP/s", "achieved": amount / per_launch_s / 1e12,
+               "peak": peak, "peak_source": f"{peak_kind} bf16 sustained"
+                                            + (" x 1.1/2.25 (TF32)" if tf else "")}
+    elif bound == "alu":
+        out = {"bound": "alu", "unit": "TFLOP/s", "achieved": amount / per_launch_s / 1e12,
+               "peak": fp32_alu, "peak_source": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
+    elif bound == "fp64":
+        out = {"bound": "alu", "unit": "TFLOP/s", "achieved": amount / per_launch_s / 1e12,
+               "peak": 1.25, "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    else:
+        out = {"bound": "hbm", "unit": "GB/s", "achieved": amount / per_launch_s / 1e9,
+               "peak": peaks["hbm_gbs"], "peak_source": f"{peak_kind} copy"}
     out["frac"] = out["achieved"] / out["peak"]
     out["kernel"] = name
     out["launch_us"] = per_launch_s * 1e6
-    out["peak_source"] = f"{peak_kind} ({'sustained' if out['bound'] == 'tensor' else 'copy'})"
     out["traffic"] = _traffic(name)
-    out["share"] = {k: round(v[0] / sum(x[0] for x in prof.values()), 4) for k, v in prof.items()}
+    total = sum(x[0] for x in prof.values())
+    out["share"] = {k: round(v[0] / total, 4) for k, v in prof.items()}
     return out
 
 
 # ---------------------------------------------------------------------- CPU oracle
-def cpu_baseline(M, a_p, c_p, dt, budget_s=CPU_BUDGET_S, replicas=CPU_SAMPLE_REPLICAS):
-    """The FP64 oracle as it stands on the host cores, on the same matrix and GLE with
-    a replica sample, every element accumulated; timed for about budget_s."""
+def _oracle(wl):
     from oracle.fth import OracleFTH
-    pairs = syn.upper_pairs(M.shape[0])
-    o = OracleFTH(M=M.astype(np.float32).astype(np.float64), a_p=a_p, c_p=c_p, dt=dt,
-                  replicas=replicas, seed=SEED, block=BLOCK, pairs=pairs)
+    R = min(wl.cpu_replicas, wl.R)
+    return OracleFTH(**wl.oracle_matrix(), a_p=wl.a_p, c_p=wl.c_p, dt=wl.dt, replicas=R,
+                     seed=wl.seed, block=wl.block, pairs=wl.element_pairs()), R
+
+
+def cpu_baseline(wl, budget_s=CPU_BUDGET_S):
+    """The FP64 oracle as it stands on the host cores, on the same matrix and GLE with
+    a replica sample and the same tracked elements; timed for about budget_s."""
+    o, R = _oracle(wl)
     o.run(1)
-    steps, t0 = 0, time.perf_counter()
+    steps, chunk, t0 = 0, 1, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        o.run(1)
-        steps += 1
+        o.run(chunk)
+        steps += chunk
+        if time.perf_counter() - t0 < 0.1 * budget_s:
+            chunk = min(chunk * 2, 4096)
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": replicas * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"N={M.shape[0]}, {replicas} replicas, all {len(pairs)} elements, "
+    return {"value": R * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{wl.name}: {R} of {wl.R} replicas, {len(wl.element_pairs())} elements, "
                       f"{steps} steps in {el:.1f} s"}
 
 
@@ -183,31 +274,28 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    M, lam, mu, a_p, c_p, dt, rep = _workload()
-    from oracle.fth import OracleFTH
-    pairs = syn.upper_pairs(N)
-    o = OracleFTH(M=M.astype(np.float32).astype(np.float64), a_p=a_p, c_p=c_p, dt=dt,
-                  replicas=CPU_SAMPLE_REPLICAS, seed=SEED, block=BLOCK, pairs=pairs)
+    wl = Workload(args.workload, args.precision)
+    o, R = _oracle(wl)
     o.run(min(max(args.warmup, 1), 2))
-    # each step is a bounded sample (CPU_SAMPLE_REPLICAS of the R replicas, all
-    # elements); the run stops after REF_BUDGET_S if K steps would take longer
+    # each step is a bounded sample (R of the workload's replicas, the same elements);
+    # the run stops after REF_BUDGET_S if K steps would take longer
     steps, t0 = 0, time.perf_counter()
     while steps < args.steps and time.perf_counter() - t0 < REF_BUDGET_S:
         o.run(1)
         steps += 1
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    value = CPU_SAMPLE_REPLICAS * steps / el
+    value = R * steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
-        "ms_per_step": el / max(steps, 1) * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "replicas_sampled": CPU_SAMPLE_REPLICAS},
+        "ms_per_step": el / max(steps, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.label, "n": wl.n, "replicas_sampled": R},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"N={N}, {CPU_SAMPLE_REPLICAS} of {R} replicas per step, "
-                                   f"all {len(pairs)} elements, {steps} steps in {el:.1f} s"},
+                         "sample": f"{wl.name}: {R} of {wl.R} replicas per step, "
+                                   f"{len(wl.element_pairs())} elements, {steps} steps in "
+                                   f"{el:.1f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -218,13 +306,17 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense4096",
+                    choices=["dense4096", "small_fp64", "lattice64"])
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 20000
         return reference_arm(args)
 
     import torch
@@ -239,12 +331,13 @@ def main():
 
     from paper_1402_2095_gb300 import FTH, build
     build.build()
-    M, lam, mu, a_p, c_p, dt, rep = _workload()
-    M32 = M.astype(np.float32)
-    Md = torch.from_numpy(M32).cuda()
+    wl = Workload(args.workload, args.precision)
+    steps = args.steps if args.steps is not None else wl.default_steps
     stream = torch.cuda.current_stream()
-    f = FTH(M=Md, a_p=a_p, c_p=c_p, dt=dt, replicas=R, seed=SEED + 7919 * rank,
-            precision=args.precision, track="all", block=BLOCK, stream=stream)
+    ctx_kw = dict(a_p=wl.a_p, c_p=wl.c_p, dt=wl.dt, replicas=wl.R, seed=wl.seed,
+                  precision=wl.precision, track=wl.track, pairs=wl.pairs, block=wl.block,
+                  stream=stream, replica_offset=rank * wl.R)
+    f = FTH(**wl.matrix_kwargs(device=True), **ctx_kw)
     f.run(args.warmup)
     torch.cuda.synchronize()
     l0 = f.info()["launches"]
@@ -255,7 +348,7 @@ def main():
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    f.run(args.steps)
+    f.run(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -269,51 +362,67 @@ def main():
     launches = f.info()["launches"] - l0
     f.poll()
 
-    # per-kernel device time, CUDA events on the launching stream (separate pass)
+    # per-kernel device time, CUDA events on each launching stream (separate pass)
+    prof_steps = min(steps, 2000)
     f.profile(True)
-    f.run(min(args.steps, 2000))
+    f.run(prof_steps)
     prof = f.profile_read()
     f.profile(False)
     peaks, peak_kind = _peaks()
-    stack_cols = (2048 // R) * R
-    roof = roofline(prof, args.precision, N, R, stack_cols, peaks, peak_kind)
+    n64 = prof.get("fp64_dense", (0.0, 1))[1]
+    info = {"stack_cols": (2048 // wl.R) * wl.R if wl.track == "all" else 4 * wl.R,
+            "steps_per_launch": prof_steps / max(n64, 1)}
+    roof = roofline(prof, wl, info, peaks, peak_kind)
 
-    # end to end through the public API with host buffers: pinned M in, results out
-    Mh = torch.from_numpy(M32).pin_memory()
-    pairs = syn.upper_pairs(N)
+    # end to end through the public API with host buffers: matrix in, results out
+    pairs = wl.element_pairs()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = FTH(M=Mh, a_p=a_p, c_p=c_p, dt=dt, replicas=R, seed=SEED + 7919 * rank + 1,
-            precision=args.precision, track="all", block=BLOCK, stream=stream)
-    g.run(args.steps)
+    g = FTH(**wl.matrix_kwargs(device=False, pinned=True), **dict(ctx_kw, seed=wl.seed + 1))
+    g.run(steps)
     vals, errs = g.elements(pairs)
     t_e2e = time.perf_counter() - t0
-    h2d = M32.nbytes + pairs.shape[0] * 8
-    d2h = pairs.shape[0] * 3 * 8
+    if wl.csr is not None:
+        h2d = wl.csr[0].nbytes + wl.csr[1].nbytes + wl.csr[2].nbytes + pairs.nbytes
+    elif wl.precision == "fp64":
+        h2d = wl.M64.nbytes
+    else:
+        h2d = wl.M32.nbytes
+    h2d += pairs.shape[0] * 8                      # element indices of the results
+    d2h = pairs.shape[0] * 3 * 8                   # (mean, M2, partial) per element
     g.close()
     del g
 
-    value = R * args.steps * world / (ms / 1e3)
+    value = wl.R * steps * world / (ms / 1e3)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "replicas_per_gpu": R, "precision": args.precision,
-                   "track": "all", "s": 4, "dt": dt, "block": BLOCK, "mu": mu,
-                   "fit_max_rel_err": rep.get("max_rel_err"),
-                   "l2": "per-step working set > L2: M %d MB + state %d MB + staged samples %d MB"
-                         " + partial sums %d MB; steps back to back" % (
-                             M32.nbytes >> 20, (8 * N * R * 4) >> 20, (N * stack_cols * 4) >> 20,
-                             ((N // 128) * (N // 128 + 1) // 2 * 128 * 128 * 4) >> 20),
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if wl.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": wl.label, "n": wl.n, "replicas_per_gpu": wl.R,
+                   "precision": wl.precision, "track": wl.track, "s": 4, "dt": wl.dt,
+                   "block": wl.block, "mu": wl.mu, "fit_max_rel_err": wl.fit.get("max_rel_err"),
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
-        "e2e": {"value": R * args.steps * world / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+        "e2e": {"value": wl.R * steps * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps},
     }
+    if wl.name == "dense4096":
+        sc = info["stack_cols"]
+        line["config"]["l2"] = (
+            "per-step working set > L2: M %d MB + state %d MB + staged samples %d MB + partial "
+            "sums %d MB; steps back to back" % (
+                wl.M32.nbytes >> 20, (8 * wl.n * wl.R * 4) >> 20, (wl.n * sc * 4) >> 20,
+                ((wl.n // 128) * (wl.n // 128 + 1) // 2 * 128 * 128 * 4) >> 20))
+    elif wl.name == "lattice64":
+        line["config"]["l2"] = "state 805 MB per step > L2 (129 MB); steps back to back"
+    else:
+        line["config"]["l2"] = ("whole problem fits on chip (N=32): FP64 state in registers and "
+                                "shared memory for the whole segment; no HBM traffic per step")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(M, a_p, c_p, dt)
+        line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -43,7 +43,7 @@ struct Layout {
     int64_t N, R, Rp, Np, nnz, stack, ps_ld, ntracked, count, nbt;
     size_t off_M = 0, off_Mlo = 0, off_rowptr = 0, off_col = 0, off_val = 0;
     size_t off_q0 = 0, off_q1 = 0, off_p = 0, off_s = 0, off_MQ = 0, off_ophi = 0, off_oplo = 0;
-    size_t off_ps = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
+    size_t off_ps = 0, off_ps1 = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
     size_t off_gidx = 0, off_gout = 0, off_err = 0;
     size_t total = 0;
 };
@@ -253,12 +253,14 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_q0 = c.take((size_t)Np * Rp * 4);
         L->off_p = c.take((size_t)Np * Rp * 4);
         L->off_s = c.take((size_t)std::max(nsub, 1) * Np * Rp * 4);
-        L->off_MQ = c.take((size_t)Np * Rp * 4);
+        // the tensor-core force may write up to kMaxForcePlanes partial planes
+        L->off_MQ = c.take((size_t)(tc ? kMaxForcePlanes : 1) * Np * Rp * 4);
         if (tc) {
             L->off_ophi = c.take((size_t)Rp * Np * esz);
             if (o->precision == FTH_PREC_BF16X3) L->off_oplo = c.take((size_t)Rp * Np * esz);
         }
         L->off_ps = c.take((size_t)Np * L->ps_ld * 4);
+        L->off_ps1 = c.take((size_t)Np * L->ps_ld * 4);
     } else if (L->path == kPathCsr) {
         L->off_rowptr = c.take((size_t)(N + 1) * 4);
         L->off_col = c.take((size_t)std::max<int64_t>(L->nnz, 1) * 4);
@@ -268,6 +270,7 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_p = c.take((size_t)N * Rp * 4);
         L->off_s = c.take((size_t)std::max(nsub, 1) * N * Rp * 4);
         L->off_ps = c.take((size_t)N * L->ps_ld * 4);
+        L->off_ps1 = c.take((size_t)N * L->ps_ld * 4);
     } else {
         L->off_M = c.take((size_t)N * Np * 8);
         L->off_q0 = c.take((size_t)L->R * Np * 8);
@@ -299,6 +302,11 @@ inline float bf16_to_f(uint16_t h) {
     std::memcpy(&f, &u, 4);
     return f;
 }
+// Offset of element (i, j) of an Np x Np matrix stored as [Np/128][Np/ks][128][ks].
+inline size_t blocked_index(int64_t i, int64_t j, int64_t Np, int64_t ks) {
+    return (size_t)((((i / 128) * (Np / ks) + j / ks) * 128 + (i % 128)) * ks + (j % ks));
+}
+
 inline float tf32_rna(float f) {
     uint32_t u;
     std::memcpy(&u, &f, 4);
@@ -335,7 +343,16 @@ struct fth_ctx {
     void *p = nullptr, *s = nullptr;
     float* MQ = nullptr;
     void *ophi = nullptr, *oplo = nullptr;
-    float* ps = nullptr;
+    float* ps = nullptr;          // sample stack being filled (one of psb)
+    float* psb[2] = {nullptr, nullptr};
+    int psi = 0;                  // index of the stack being filled
+    // accumulation passes and block flushes run on a side stream, overlapping the next
+    // steps; events order them against the caller's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_join = nullptr;
+    bool free_pending[2] = {false, false};
+    bool side_used = false;
     int32_t* pairs = nullptr;
     void* partial = nullptr;
     double *mean = nullptr, *m2 = nullptr;
@@ -344,6 +361,7 @@ struct fth_ctx {
     uint32_t* err = nullptr;
     TcForce* tcf = nullptr;
     TcSyrk* tcs = nullptr;
+    TcSyrk* tcs1 = nullptr;
     // host-side bookkeeping
     std::unordered_map<uint64_t, int64_t> pair_index;
     int64_t t = 0, nsamp = 0, accumulated = 0, inblock = 0, nfill = 0, nblocks = 0, launches = 0;
@@ -396,14 +414,18 @@ cudaEvent_t prof_event(fth_ctx* c) {
 struct ProfScope {
     fth_ctx* c;
     bool on;
-    ProfScope(fth_ctx* ctx, int cls) : c(ctx), on(ctx->prof) {
+    cudaStream_t st;
+    size_t idx = 0;
+    ProfScope(fth_ctx* ctx, int cls, cudaStream_t s = nullptr)
+        : c(ctx), on(ctx->prof), st(s ? s : ctx->stream) {
         if (!on) return;
         fth_ctx::ProfRec r{cls, prof_event(c), prof_event(c)};
-        cudaEventRecord(r.a, c->stream);
+        cudaEventRecord(r.a, st);
+        idx = c->prof_recs.size();
         c->prof_recs.push_back(r);
     }
     ~ProfScope() {
-        if (on) cudaEventRecord(c->prof_recs.back().b, c->stream);
+        if (on) cudaEventRecord(c->prof_recs[idx].b, st);
     }
 };
 
@@ -426,28 +448,61 @@ fth_status force(fth_ctx* c) {
     return FTH_OK;
 }
 
+// Before the first sample of a stack is written: the pass that read this stack two
+// batches ago must be finished.
+fth_status claim_stack(fth_ctx* c) {
+    if (c->free_pending[c->psi]) {
+        FTH_CK(cudaStreamWaitEvent(c->stream, c->ev_free[c->psi], 0), "wait stack");
+        c->free_pending[c->psi] = false;
+    }
+    c->ps = c->psb[c->psi];
+    return FTH_OK;
+}
+
+// One accumulation pass over the filled stack, on the side stream; the other stack
+// takes the next samples meanwhile.
 fth_status accumulate(fth_ctx* c) {
     const Layout& L = c->L;
     if (c->nfill == 0) return FTH_OK;
     const int64_t ncols = c->nfill * L.Rp;
-    ProfScope ps(c, L.track == FTH_TRACK_ALL ? (is_tc(c) ? FTH_K_SYRK_TC : FTH_K_SYRK_FP32)
-                                             : FTH_K_PAIR_ACCUM);
-    if (L.track == FTH_TRACK_ALL) {
-        if (is_tc(c)) {
-            FTH_CK(tc_syrk_run(c->tcs, ncols, static_cast<float*>(c->partial), c->err, c->stream),
-                   "tc syrk");
+    const int b = c->psi;
+    FTH_CK(cudaEventRecord(c->ev_filled[b], c->stream), "record filled");
+    FTH_CK(cudaStreamWaitEvent(c->side, c->ev_filled[b], 0), "side wait");
+    c->side_used = true;
+    {
+        ProfScope ps(c, L.track == FTH_TRACK_ALL ? (is_tc(c) ? FTH_K_SYRK_TC : FTH_K_SYRK_FP32)
+                                                 : FTH_K_PAIR_ACCUM,
+                     c->side);
+        if (L.track == FTH_TRACK_ALL) {
+            if (is_tc(c)) {
+                FTH_CK(tc_syrk_run(b ? c->tcs1 : c->tcs, ncols, static_cast<float*>(c->partial),
+                                   c->err, c->side),
+                       "tc syrk");
+            } else {
+                FTH_CK(launch_syrk_fp32(c->psb[b], L.ps_ld, ncols, L.Np,
+                                        static_cast<float*>(c->partial), c->side),
+                       "syrk");
+            }
         } else {
-            FTH_CK(launch_syrk_fp32(c->ps, L.ps_ld, ncols, L.Np, static_cast<float*>(c->partial),
-                                    c->stream),
-                   "syrk");
+            FTH_CK(launch_pair_accum(c->psb[b], L.ps_ld, ncols, c->pairs, L.ntracked,
+                                     static_cast<float*>(c->partial), c->side),
+                   "pair accumulate");
         }
-    } else {
-        FTH_CK(launch_pair_accum(c->ps, L.ps_ld, ncols, c->pairs, L.ntracked,
-                                 static_cast<float*>(c->partial), c->stream),
-               "pair accumulate");
     }
+    FTH_CK(cudaEventRecord(c->ev_free[b], c->side), "record free");
+    c->free_pending[b] = true;
     ++c->launches;
     c->nfill = 0;
+    c->psi ^= 1;
+    return FTH_OK;
+}
+
+// The caller's stream waits for everything queued on the side stream.
+fth_status join_side(fth_ctx* c) {
+    if (!c->side_used) return FTH_OK;
+    FTH_CK(cudaEventRecord(c->ev_join, c->side), "record join");
+    FTH_CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
+    c->side_used = false;
     return FTH_OK;
 }
 
@@ -455,21 +510,26 @@ fth_status flush(fth_ctx* c) {
     const Layout& L = c->L;
     const double inv = 1.0 / ((double)c->block * (double)L.R);
     const double nb = (double)(c->nblocks + 1);
-    ProfScope ps(c, FTH_K_FLUSH);
     if (L.path == kPathDense64) {
+        ProfScope ps(c, FTH_K_FLUSH);
         FTH_CK(launch_flush64(static_cast<double*>(c->partial), L.R, L.count, c->mean, c->m2,
                               L.count, inv, nb, c->err, c->stream),
                "flush64");
     } else {
+        // after the block's last accumulation pass, on the same (side) stream
+        ProfScope ps(c, FTH_K_FLUSH, c->side);
         FTH_CK(launch_flush(static_cast<float*>(c->partial), c->mean, c->m2, L.count, inv, nb,
-                            c->err, c->stream),
+                            c->err, c->side),
                "flush");
+        c->side_used = true;
     }
     ++c->launches;
     ++c->nblocks;
     c->inblock = 0;
     return FTH_OK;
 }
+
+int mq_planes(const fth_ctx* c) { return c->tcf ? tc_force_planes(c->tcf) : 1; }
 
 void op_ptrs(fth_ctx* c, int& kind, void*& hi, void*& lo) {
     kind = kOpNone;
@@ -492,25 +552,32 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
     if (!c->primed) {
         fth_status st = force(c);
         if (st != FTH_OK) return st;
-        ProfScope ps(c, FTH_K_GLE_DENSE);
-        FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s, (uint32_t)c->t,
-                                kDoStart, c->observable, c->ps, L.ps_ld, 0, opk, hi, lo, L.Np,
-                                c->stream),
-               "gle prologue");
+        {
+            ProfScope ps(c, FTH_K_GLE_DENSE);
+            FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, mq_planes(c), q, p, s,
+                                    (uint32_t)c->t, kDoStart, c->observable, c->ps, L.ps_ld, 0,
+                                    opk, hi, lo, L.Np, c->stream),
+                   "gle prologue");
+        }
         ++c->launches;
         c->primed = 1;
     }
     for (int64_t k = 0; k < steps; ++k) {
+        const uint32_t kappa = (uint32_t)(c->t + 1);
         fth_status st = force(c);
         if (st != FTH_OK) return st;
         const bool take = c->nsamp >= c->burnin;
         const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0);
+        if (take && c->nfill == 0) {
+            st = claim_stack(c);
+            if (st != FTH_OK) return st;
+        }
         {
-        ProfScope ps(c, FTH_K_GLE_DENSE);
-        FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, q, p, s,
-                                (uint32_t)(c->t + 1), flags, c->observable, c->ps, L.ps_ld,
-                                c->nfill, opk, hi, lo, L.Np, c->stream),
-               "gle step");
+            ProfScope ps(c, FTH_K_GLE_DENSE);
+            FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, mq_planes(c), q, p, s,
+                                    kappa, flags, c->observable, c->ps, L.ps_ld, c->nfill, opk,
+                                    hi, lo, L.Np, c->stream),
+                   "gle step");
         }
         ++c->launches;
         ++c->t;
@@ -529,7 +596,9 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
             }
         }
     }
-    return accumulate(c);
+    fth_status st = accumulate(c);
+    if (st != FTH_OK) return st;
+    return join_side(c);
 }
 
 fth_status run_csr(fth_ctx* c, int64_t steps) {
@@ -555,6 +624,10 @@ fth_status run_csr(fth_ctx* c, int64_t steps) {
     }
     for (int64_t k = 0; k < steps; ++k) {
         const bool take = c->nsamp >= c->burnin;
+        if (take && c->nfill == 0) {
+            fth_status st0 = claim_stack(c);
+            if (st0 != FTH_OK) return st0;
+        }
         fth_status st = launch(kDoEnd | kDoStart | (take ? kDoSample : 0), (uint32_t)(c->t + 1));
         if (st != FTH_OK) return st;
         ++c->t;
@@ -573,7 +646,9 @@ fth_status run_csr(fth_ctx* c, int64_t steps) {
             }
         }
     }
-    return accumulate(c);
+    fth_status st = accumulate(c);
+    if (st != FTH_OK) return st;
+    return join_side(c);
 }
 
 fth_status run_dense64(fth_ctx* c, int64_t steps) {
@@ -718,6 +793,7 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     c->g32.key0 = c->g64.key0 = (uint32_t)opt->seed;
     c->g32.key1 = c->g64.key1 = (uint32_t)(opt->seed >> 32);
     c->g32.roff = c->g64.roff = (uint32_t)opt->replica_offset;
+    set_round_keys(c->g32);
 
     auto at = [&](size_t off) { return static_cast<void*>(c->ws + off); };
     c->M = at(L.off_M);
@@ -729,7 +805,9 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     c->MQ = L.off_MQ ? static_cast<float*>(at(L.off_MQ)) : nullptr;
     c->ophi = L.off_ophi ? at(L.off_ophi) : nullptr;
     c->oplo = L.off_oplo ? at(L.off_oplo) : nullptr;
-    c->ps = L.off_ps ? static_cast<float*>(at(L.off_ps)) : nullptr;
+    c->psb[0] = L.off_ps ? static_cast<float*>(at(L.off_ps)) : nullptr;
+    c->psb[1] = L.off_ps1 ? static_cast<float*>(at(L.off_ps1)) : nullptr;
+    c->ps = c->psb[0];
     c->pairs = static_cast<int32_t*>(at(L.off_pairs));
     c->partial = at(L.off_partial);
     c->mean = static_cast<double*>(at(L.off_mean));
@@ -745,9 +823,7 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
 
     auto bail = [&](fth_status s2) {
         g_thread_error = c->last_error;
-        if (c->tcf) tc_force_free(c->tcf);
-        if (c->tcs) tc_syrk_free(c->tcs);
-        delete c;
+        fth_destroy(c);
         return s2;
     };
 #define FTH_CK_C(call, what)                                \
@@ -757,6 +833,16 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     } while (0)
 
     FTH_CK_C(cudaMemsetAsync(c->ws, 0, L.total, c->stream), "zero workspace");
+    if (L.path != kPathDense64) {
+        int lo = 0, hi = 0;
+        FTH_CK_C(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+        FTH_CK_C(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo), "side stream");
+        for (int b = 0; b < 2; ++b) {
+            FTH_CK_C(cudaEventCreateWithFlags(&c->ev_filled[b], cudaEventDisableTiming), "event");
+            FTH_CK_C(cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming), "event");
+        }
+        FTH_CK_C(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+    }
 
     // ---- M: bring to host FP64 (validation, conversion), then upload
     const int64_t N = L.N;
@@ -793,24 +879,28 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
             FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream), "h2d M");
             FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
         } else if (L.precision == FTH_PREC_BF16X3) {
+            // blocked [Np/128][Np/64][128][64]: each tensor-memory A box is contiguous
             std::vector<uint16_t> h((size_t)Np * Np, 0), l((size_t)Np * Np, 0);
             for (int64_t i = 0; i < N; ++i)
                 for (int64_t j = 0; j < N; ++j) {
                     const float x = (float)m[i * N + j];
                     const uint16_t hb = bf16_rne(x);
-                    h[i * Np + j] = hb;
-                    l[i * Np + j] = bf16_rne(x - bf16_to_f(hb));
+                    const size_t at = blocked_index(i, j, Np, 64);
+                    h[at] = hb;
+                    l[at] = bf16_rne(x - bf16_to_f(hb));
                 }
             FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M hi");
             FTH_CK_C(cudaMemcpyAsync(c->Mlo, l.data(), l.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M lo");
             FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
         } else {
+            // FP32 path: row-major [Np][Np]; TF32 path: blocked [Np/128][Np/32][128][32]
             std::vector<float> h((size_t)Np * Np, 0.f);
             const bool tf = L.precision == FTH_PREC_TF32;
             for (int64_t i = 0; i < N; ++i)
                 for (int64_t j = 0; j < N; ++j) {
                     const float x = (float)m[i * N + j];
-                    h[i * Np + j] = tf ? tf32_rna(x) : x;
+                    if (tf) h[blocked_index(i, j, Np, 32)] = tf32_rna(x);
+                    else h[i * Np + j] = x;
                 }
             FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d M");
             FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
@@ -898,8 +988,10 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
         const int kind = L.precision == FTH_PREC_TF32 ? 1 : 2;
         FTH_CK_C(tc_force_prepare(&c->tcf, kind, c->M, c->Mlo, c->ophi, c->oplo, L.Np, L.Rp, L.N, L.R),
                  "tensor maps (force)");
-        if (L.track == FTH_TRACK_ALL)
-            FTH_CK_C(tc_syrk_prepare(&c->tcs, c->ps, L.Np, L.ps_ld), "tensor maps (syrk)");
+        if (L.track == FTH_TRACK_ALL) {
+            FTH_CK_C(tc_syrk_prepare(&c->tcs, c->psb[0], L.Np, L.ps_ld), "tensor maps (syrk)");
+            FTH_CK_C(tc_syrk_prepare(&c->tcs1, c->psb[1], L.Np, L.ps_ld), "tensor maps (syrk)");
+        }
     }
 #undef FTH_CK_C
     *out = c;
@@ -1109,6 +1201,16 @@ fth_status fth_profile_read(fth_ctx* c, double* ms, int64_t* launches) {
 
 void fth_destroy(fth_ctx* c) {
     if (!c) return;
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->ev_filled[b]) cudaEventDestroy(c->ev_filled[b]);
+        if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
+    }
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->tcs1) tc_syrk_free(c->tcs1);
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

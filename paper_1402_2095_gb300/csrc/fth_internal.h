@@ -19,7 +19,16 @@ struct GleF32 {
     float dt, hdt;
     uint32_t key0, key1;
     uint32_t roff;   // replica offset in the noise counter
+    uint32_t rk[20]; // Philox round keys: key + j * (0x9E3779B9, 0xBB67AE85), j = 0..9
 };
+
+// Fills g.rk from g.key0, g.key1.
+inline void set_round_keys(GleF32& g) {
+    for (int j = 0; j < 10; ++j) {
+        g.rk[2 * j] = g.key0 + (uint32_t)j * 0x9E3779B9u;
+        g.rk[2 * j + 1] = g.key1 + (uint32_t)j * 0xBB67AE85u;
+    }
+}
 
 struct GleF64 {
     double T[kMaxNs * kMaxNs];
@@ -41,7 +50,8 @@ enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
 // ------------------------------------------------------------------ kernels
 // Dense path, state planes [Np][Rp] FP32 (replica fastest), MQ = M q (positive).
 cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
-                             const float* MQ, float* q, float* p, float* s, uint32_t kappa,
+                             const float* MQ, int mq_planes, float* q, float* p, float* s,
+                             uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
                              cudaStream_t st);
@@ -104,6 +114,9 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st);
 void tc_force_free(TcForce* tf);
+// Number of partial planes MQ[0..planes) the force kernel writes (summed by the GLE kernel).
+int tc_force_planes(const TcForce* tf);
+constexpr int kMaxForcePlanes = 4;
 
 struct TcSyrk;
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);

@@ -16,40 +16,60 @@
 
 namespace fth {
 
+// Philox4x32-10 with the round keys precomputed (rk[2j], rk[2j+1] = key + j * Weyl),
+// e.g. from a kernel parameter, so the XORs take them as constant operands.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * round], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * round + 1], (uint32_t)p0);
+    }
+    return c;
+}
+
+// One 32x32 -> 64-bit multiply per S-box gives both halves.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
     return c;
 }
 
+// u = ((x >> 9) * 2 + 1) * 2^-24, built from bits: 1 + (x >> 9) 2^-23 is exact as a
+// float, and subtracting 1 - 2^-24 is exact (Sterbenz: both operands within a factor 2).
 __device__ __forceinline__ float open_unit(uint32_t x) {
-    return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8f;  // * 2^-24
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.999999940395355224609375f;
 }
 
+// rho = sqrt(-2 ln u_a) with the accurate logf (near u = 1 the approximate log's
+// absolute error would dominate rho); the angle 2 pi u_b is shifted by pi into
+// (-pi, pi), where the hardware sine/cosine are accurate to ~2^-21 absolute, and the
+// shift is undone by the sign: cos(2 pi u) = -cos(2 pi (u - 1/2)), same for sin.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
-    const float rho = sqrtf(-2.0f * logf(open_unit(a)));
+    const float r2 = -2.0f * logf(open_unit(a));
+    const float rho = r2 * rsqrtf(fmaxf(r2, 1e-30f));
     float sn, cs;
-    sincospif(2.0f * open_unit(b), &sn, &cs);
-    z0 = rho * cs;
-    z1 = rho * sn;
+    __sincosf(6.28318530717958648f * (open_unit(b) - 0.5f), &sn, &cs);
+    z0 = -rho * cs;
+    z1 = -rho * sn;
 }
 
 // The 2*NS normals of (kappa, i, r).
 template <int NS>
-__device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t r, uint32_t k0,
-                                            uint32_t k1, float (&xi)[2 * NS]) {
+__device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t r,
+                                            const uint32_t* rk, float (&xi)[2 * NS]) {
     constexpr int kCalls = (2 * NS + 3) / 4;
 #pragma unroll
     for (int k = 0; k < kCalls; ++k) {
-        const uint4 x = philox4x32_10(make_uint4(kappa, i, r, (uint32_t)k), k0, k1);
+        const uint4 x = philox4x32_10_rk(make_uint4(kappa, i, r, (uint32_t)k), rk);
         float z[4];
         box_muller(x.x, x.y, z[0], z[1]);
         box_muller(x.z, x.w, z[2], z[3]);
@@ -57,17 +77,6 @@ __device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t
         for (int j = 0; j < 4; ++j)
             if (4 * k + j < 2 * NS) xi[4 * k + j] = z[j];
     }
-}
-
-// Only the normals of one half: first (end of step) or second (start of step).
-template <int NS>
-__device__ __forceinline__ void gle_normals_half(uint32_t kappa, uint32_t i, uint32_t r,
-                                                 uint32_t k0, uint32_t k1, int second,
-                                                 float (&xi)[NS]) {
-    float all[2 * NS];
-    gle_normals<NS>(kappa, i, r, k0, k1, all);
-#pragma unroll
-    for (int j = 0; j < NS; ++j) xi[j] = second ? all[NS + j] : all[j];
 }
 
 // v <- T v + S xi on v = (p, s_1..s_{NS-1}), with T passed as D = T - I: the

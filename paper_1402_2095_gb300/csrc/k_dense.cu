@@ -22,8 +22,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 // transposed operand stores (q^T[r][i]) are coalesced, and every thread moves one
 // 16-byte vector per plane.
 template <int NS>
-__global__ void __launch_bounds__(256)
-dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
+__global__ void __launch_bounds__(256, 3)
+dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, int mq_planes,
                  float* __restrict__ q, float* __restrict__ p, float* __restrict__ s,
                  uint32_t kappa, int flags, int observable, float* __restrict__ ps,
                  int64_t ps_ld, int64_t slot_off, int op_kind, void* op_hi, void* op_lo,
@@ -34,7 +34,15 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
     const int64_t plane = (int64_t)Np * Rp;
     const int64_t off = (int64_t)i * Rp + r0;
 
-    const float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
+    // the force may arrive as partial sums over K (one plane per K share)
+    float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
+    for (int pl = 1; pl < mq_planes; ++pl) {
+        const float4 x = *reinterpret_cast<const float4*>(MQ + pl * plane + off);
+        mq4.x += x.x;
+        mq4.y += x.y;
+        mq4.z += x.z;
+        mq4.w += x.w;
+    }
     float4 q4 = *reinterpret_cast<const float4*>(q + off);
     float4 v4[NS];
     v4[0] = *reinterpret_cast<const float4*>(p + off);
@@ -52,7 +60,7 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[2 * NS];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.key0, g.key1, xi);
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.rk, xi);
         gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
@@ -81,18 +89,19 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ,
 }
 
 cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
-                             const float* MQ, float* q, float* p, float* s, uint32_t kappa,
+                             const float* MQ, int mq_planes, float* q, float* p, float* s,
+                             uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
                              cudaStream_t st) {
     dim3 block(32, 8);
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((Rp / 4 + 7) / 8));
     const int64_t slot_off = slot * Rp;
-#define FTH_DENSE_CASE(NSV)                                                                  \
-    case NSV:                                                                                \
-        dense_gle_kernel<NSV><<<grid, block, 0, st>>>(g, (int)N, (int)R, (int)Rp, MQ, q, p, s, \
-                                                      kappa, flags, observable, ps, ps_ld,    \
-                                                      slot_off, op_kind, op_hi, op_lo, (int)Np); \
+#define FTH_DENSE_CASE(NSV)                                                                   \
+    case NSV:                                                                                 \
+        dense_gle_kernel<NSV><<<grid, block, 0, st>>>(                                        \
+            g, (int)N, (int)R, (int)Rp, MQ, mq_planes, q, p, s, kappa, flags, observable,     \
+            ps, ps_ld, slot_off, op_kind, op_hi, op_lo, (int)Np);                             \
         break;
     switch (ns) {
         FTH_DENSE_CASE(1)

@@ -19,7 +19,7 @@ namespace fth {
 // -------------------------------------------------------------- CSR fused step
 // Thread t -> (row i = t / (Rp/4), replicas 4 * (t % (Rp/4)) .. +3).
 template <int NS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 csr_step_kernel(GleF32 g, int N, int R, int Rp, const int32_t* __restrict__ rowptr,
                 const int32_t* __restrict__ col, const float* __restrict__ val,
                 const float* __restrict__ q_in, float* __restrict__ q_out,
@@ -60,7 +60,7 @@ csr_step_kernel(GleF32 g, int N, int R, int Rp, const int32_t* __restrict__ rowp
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[2 * NS];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.key0, g.key1, xi);
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.rk, xi);
         gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];

@@ -79,6 +79,17 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
         : "memory");
 }
 
+// 3-D box load; used for M stored blocked as [row block][K slice][128 rows][128 bytes],
+// where one box (x = 0, y = 0, z = block) is one contiguous 16 KiB chunk of HBM.
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8 rows x 128 B atoms,
 // atoms 1024 B apart), tcgen05 descriptor version 1.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -160,11 +171,12 @@ struct TcMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
+// a_blocks > 0: A is the blocked 3-D map with a_blocks K slices per row block.
 template <int KIND, int BN, int STAGES>
 __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b_row,
                                             int nslices, uint8_t* stages, uint64_t* full,
                                             uint64_t* empty, uint64_t* done, uint32_t tmem,
-                                            uint32_t* err) {
+                                            uint32_t* err, int slice0 = 0, int a_blocks = 0) {
     using C = TcCfg<KIND, BN>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
@@ -177,11 +189,14 @@ __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b
             if (!ok) break;
             uint8_t* base = stages + st * C::kStageBytes;
             mbar_expect_tx(&full[st], C::kStageBytes);
-            const int x = kb * C::kKPerSlice;
-            tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
+            const int x = (slice0 + kb) * C::kKPerSlice;
+            const int blk = (a_row / 128) * a_blocks + slice0 + kb;
+            if (a_blocks > 0) tma_load_3d(&maps.a_hi, &full[st], base, 0, 0, blk);
+            else tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
             tma_load_2d(&maps.b_hi, &full[st], base + C::kABytes, x, b_row);
             if (KIND == 2) {
-                tma_load_2d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, x, a_row);
+                if (a_blocks > 0) tma_load_3d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, 0, 0, blk);
+                else tma_load_2d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, x, a_row);
                 tma_load_2d(&maps.b_lo, &full[st], base + 2 * C::kABytes + C::kBBytes, x, b_row);
             }
             ++issued;
@@ -288,7 +303,8 @@ tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int
     uint32_t tmem;
     tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
     const int row0 = blockIdx.x * 128, col0 = blockIdx.y * BN;
-    tc_mainloop<KIND, BN, STAGES>(maps, row0, col0, nslices, stages, full, empty, done, tmem, err);
+    tc_mainloop<KIND, BN, STAGES>(maps, row0, col0, nslices, stages, full, empty, done, tmem, err,
+                                  0, nslices);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -309,6 +325,94 @@ tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int
             }
         }
     }
+    tc_teardown<KIND, BN>(tmem);
+}
+
+// ------------------------------------------------------------------ split-K force GEMM
+// The replicas of one 128-row block fit one tile (BN >= Rp).  The K range is split over
+// the KSPLIT CTAs of a (1, KSPLIT, 1) cluster; each accumulates its K share in TMEM,
+// stages the 128 x BN partial in its (now idle) shared memory, and after a cluster
+// barrier reduces one BN/KSPLIT-column quarter of the tile across the cluster through
+// distributed shared memory and writes it.  A second cluster barrier keeps every
+// partial alive until all peers have read it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t local_saddr, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_saddr), "r"(rank));
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(remote)
+                 : "memory");
+    return v;
+}
+
+template <int KIND, int BN, int STAGES, int KSPLIT>
+__global__ void __launch_bounds__(128, 1)
+tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int ldf,
+                       int N, int Rp, int nslices_total, uint32_t* err) {
+    constexpr int LDS = BN + 4;                 // padded row of the staged partial
+    static_assert(STAGES * TcCfg<KIND, BN>::kStageBytes >= 128 * LDS * 4, "stage space");
+    uint8_t* stages;
+    uint64_t *full, *empty, *done;
+    uint32_t tmem;
+    tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
+    const int row0 = blockIdx.x * 128;
+    const int kc = (int)cluster_rank();
+    const int s0 = (nslices_total * kc) / KSPLIT;
+    const int s1 = (nslices_total * (kc + 1)) / KSPLIT;
+    tc_mainloop<KIND, BN, STAGES>(maps, row0, 0, s1 - s0, stages, full, empty, done, tmem, err,
+                                  s0, nslices_total);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    float* red = reinterpret_cast<float*>(stages);
+    const int row = warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < BN / 16; ++c) {
+        float v[16];
+        if (s1 > s0) {
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        float4* dst = reinterpret_cast<float4*>(red + row * LDS + c * 16);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+    cluster_sync_all();
+    constexpr int QW = BN / KSPLIT;             // columns reduced by this CTA
+    constexpr int Q4 = QW / 4;
+    const uint32_t red_s = smem_u32(red);
+    for (int f = threadIdx.x; f < 128 * Q4; f += 128) {
+        const int r = f / Q4;
+        const int col = kc * QW + 4 * (f % Q4);
+        const uint32_t off = red_s + (uint32_t)((r * LDS + col) * 4);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int src = 0; src < KSPLIT; ++src) {
+            const float4 x = ld_cluster_f4(off, (uint32_t)src);
+            acc.x += x.x;
+            acc.y += x.y;
+            acc.z += x.z;
+            acc.w += x.w;
+        }
+        if (ok && row0 + r < N && col + 4 <= Rp)
+            *reinterpret_cast<float4*>(MQ + (int64_t)(row0 + r) * ldf + col) = acc;
+    }
+    cluster_sync_all();
     tc_teardown<KIND, BN>(tmem);
 }
 
@@ -354,6 +458,56 @@ tc_syrk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, i
     tc_teardown<1, 128>(tmem);
 }
 
+// 128 x 256 tiles: rows I*128.., columns J'*256.. covering packed tiles (I, 2J') and
+// (I, 2J'+1); only the tiles on or above the diagonal are accumulated.  Half the CTAs
+// of the 128 x 128 form and 25 % fewer operand bytes per flop.
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1)
+tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, int nbt,
+                    int nslices, uint32_t* err) {
+    uint8_t* stages;
+    uint64_t *full, *empty, *done;
+    uint32_t tmem;
+    tc_setup<1, 256, STAGES>(stages, full, empty, done, tmem);
+    const int nbw = (nbt + 1) / 2;
+    int t = blockIdx.x, I = 0;
+    while (t >= nbw - I / 2) {
+        t -= nbw - I / 2;
+        ++I;
+    }
+    const int Jw = I / 2 + t;
+    tc_mainloop<1, 256, STAGES>(maps, I * 128, Jw * 256, nslices, stages, full, empty, done, tmem,
+                                err);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    if (ok) {
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const int J = 2 * Jw + half;
+            if (J < I || J >= nbt) continue;
+            const int64_t tile = (int64_t)I * nbt - ((int64_t)I * (I - 1)) / 2 + (J - I);
+            float* out = tiles + tile * 128 * 128 + (int64_t)(warp * 32 + lane) * 128;
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 128 + c * 16), v);
+                float4* dst = reinterpret_cast<float4*>(out + c * 16);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float4 o = dst[j];
+                    o.x += v[4 * j];
+                    o.y += v[4 * j + 1];
+                    o.z += v[4 * j + 2];
+                    o.w += v[4 * j + 3];
+                    dst[j] = o;
+                }
+            }
+        }
+    }
+    tc_teardown<1, 256>(tmem);
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -385,9 +539,29 @@ cudaError_t make_map(CUtensorMap* map, const void* base, int bf16, uint64_t cols
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 3-D map of M stored blocked: [Np/128][Np/KS][128][KS], KS = 128 bytes of K.
+cudaError_t make_blocked_map(CUtensorMap* map, const void* base, int bf16, uint64_t Np) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const uint32_t esz = bf16 ? 2 : 4;
+    const uint64_t ks = 128 / esz;
+    const cuuint64_t dims[3] = {ks, 128, (Np / 128) * (Np / ks)};
+    const cuuint64_t strides[2] = {ks * esz, 128 * ks * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)ks, 128, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 constexpr int kForceBN = 64;
 constexpr int kForceStages = 6;
-constexpr int kSyrkStages = 4;
+constexpr int kSyrkStages = 6;
+constexpr int kSyrkWideStages = 4;
+constexpr int kWideBN = 256;
+constexpr int kKSplit = 4;
 
 template <int KIND, int BN, int STAGES>
 size_t tc_smem_bytes() {
@@ -397,13 +571,16 @@ size_t tc_smem_bytes() {
 }  // namespace
 
 struct TcForce {
-    TcMaps maps;
+    TcMaps maps;        // B box of kForceBN rows (column-tiled kernel)
+    TcMaps maps_wide;   // B box of kWideBN rows (split-K kernel, Rp <= kWideBN)
     int kind;
+    bool wide;
     int64_t Np, Rp, N, R;
 };
 
 struct TcSyrk {
-    TcMaps maps;
+    TcMaps maps;        // A and B boxes of 128 rows
+    TcMaps maps_wide;   // B box of 256 rows (Np >= 256)
     int64_t Np, ps_ld;
 };
 
@@ -417,14 +594,23 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
     tf->N = N;
     tf->R = R;
     const int bf = kind == 2;
-    cudaError_t e = make_map(&tf->maps.a_hi, A_hi, bf, Np, Np, Np, 128);
+    cudaError_t e = make_blocked_map(&tf->maps.a_hi, A_hi, bf, Np);
     if (e == cudaSuccess) e = make_map(&tf->maps.b_hi, B_hi, bf, Np, Rp, Np, kForceBN);
-    if (e == cudaSuccess && bf) e = make_map(&tf->maps.a_lo, A_lo, bf, Np, Np, Np, 128);
+    if (e == cudaSuccess && bf) e = make_blocked_map(&tf->maps.a_lo, A_lo, bf, Np);
     if (e == cudaSuccess && bf) e = make_map(&tf->maps.b_lo, B_lo, bf, Np, Rp, Np, kForceBN);
     if (!bf) {
         tf->maps.a_lo = tf->maps.a_hi;
         tf->maps.b_lo = tf->maps.b_hi;
     }
+    // replicas of a row block fit one 256-wide tile: split-K cluster kernel
+    tf->wide = Rp > 128 && Rp <= kWideBN;
+    if (e == cudaSuccess && tf->wide) {
+        tf->maps_wide = tf->maps;
+        e = make_map(&tf->maps_wide.b_hi, B_hi, bf, Np, Rp, Np, kWideBN);
+        if (e == cudaSuccess && bf) e = make_map(&tf->maps_wide.b_lo, B_lo, bf, Np, Rp, Np, kWideBN);
+        if (!bf) tf->maps_wide.b_lo = tf->maps_wide.b_hi;
+    }
+
     if (e != cudaSuccess) {
         delete tf;
         return e;
@@ -433,8 +619,38 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
     return cudaSuccess;
 }
 
+template <int KIND, int STAGES>
+static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
+                                 cudaStream_t st) {
+    const size_t sm = tc_smem_bytes<KIND, kWideBN, STAGES>();
+    auto kern = tc_force_splitk_kernel<KIND, kWideBN, STAGES, kKSplit>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(tf->Np / 128), kKSplit, 1);
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = kKSplit;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int nslices = (int)(KIND == 1 ? tf->Np / 32 : tf->Np / 64);
+    return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
+                              nslices, err);
+}
+
+int tc_force_planes(const TcForce*) { return 1; }
+
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st) {
+    if (tf->wide) {
+        cudaError_t e = tf->kind == 1 ? launch_splitk<1, 4>(tf, MQ, ldf, err, st)
+                                      : launch_splitk<2, 2>(tf, MQ, ldf, err, st);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     dim3 grid((unsigned)(tf->Np / 128), (unsigned)((tf->Rp + kForceBN - 1) / kForceBN));
     if (tf->kind == 1) {
         constexpr int K = 1;
@@ -469,6 +685,14 @@ cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t p
     ts->maps.b_hi = ts->maps.a_hi;
     ts->maps.a_lo = ts->maps.a_hi;
     ts->maps.b_lo = ts->maps.a_hi;
+    ts->maps_wide = ts->maps;
+    if (Np >= 256) {
+        e = make_map(&ts->maps_wide.b_hi, ps, 0, ps_ld, Np, ps_ld, 256);
+        if (e != cudaSuccess) {
+            delete ts;
+            return e;
+        }
+    }
     *out = ts;
     return cudaSuccess;
 }
@@ -477,11 +701,21 @@ cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t*
                         cudaStream_t st) {
     if (ncols <= 0) return cudaSuccess;
     const int nbt = (int)(ts->Np / 128);
+    const int nslices = (int)((ncols + 31) / 32);
+    if (ts->Np >= 256) {
+        const int nbw = (nbt + 1) / 2;
+        unsigned nctas = 0;
+        for (int I = 0; I < nbt; ++I) nctas += (unsigned)(nbw - I / 2);
+        const size_t sm = tc_smem_bytes<1, 256, kSyrkWideStages>();
+        auto kern = tc_syrk_wide_kernel<kSyrkWideStages>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<nctas, 128, sm, st>>>(ts->maps_wide, tiles, nbt, nslices, err);
+        return cudaGetLastError();
+    }
     const unsigned ntiles = (unsigned)(nbt * (nbt + 1) / 2);
     const size_t sm = tc_smem_bytes<1, 128, kSyrkStages>();
     auto kern = tc_syrk_kernel<kSyrkStages>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const int nslices = (int)((ncols + 31) / 32);
     kern<<<ntiles, 128, sm, st>>>(ts->maps, tiles, nbt, nslices, err);
     return cudaGetLastError();
 }

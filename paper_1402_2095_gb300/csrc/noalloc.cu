@@ -121,13 +121,14 @@ extern "C" fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t 
     g.key0 = (uint32_t)seed;
     g.key1 = (uint32_t)(seed >> 32);
     g.roff = 0;
+    set_round_keys(g);
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
 
     dim3 grid((unsigned)((n + 63) / 64), (unsigned)((ldr + 63) / 64));
     noalloc_force_kernel<<<grid, 256, 0, strm>>>(M, ldm, q, ldr, mq, (int)n);
     if (cudaGetLastError() != cudaSuccess) return FTH_E_CUDA;
     const int flags = mode == 1 ? kDoStart : (kDoEnd | kDoStart | (sample ? kDoSample : 0));
-    if (launch_dense_gle(ns, g, n, replicas, ldr, mq, q, p, s, kappa, flags, FTH_OBS_P, sample,
+    if (launch_dense_gle(ns, g, n, replicas, ldr, mq, 1, q, p, s, kappa, flags, FTH_OBS_P, sample,
                          ldr, 0, kOpNone, nullptr, nullptr, n, strm) != cudaSuccess)
         return FTH_E_CUDA;
     return FTH_OK;
