@@ -8,12 +8,13 @@ GEMM in the chosen precision (TF32 by default), every element of <p p^T> accumul
 (FP32 block partials, FP64 block sums).  One step = force, B, O, sample + accumulate,
 O, B, A over all replicas.
 
-Other workloads (--workload): small_fp64 (N = 32 dense FP64, R = 16, all elements) and
+Other workloads (--workload): small_fp64 (N = 32 dense FP64, R = 16, all elements),
 lattice64 (64^3 periodic lattice, CSR FP32, R = 64, diagonal + nearest-neighbour
-elements).
+elements) and ragged512 (512 dense problems of ragged order in one problem pool).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload dense4096|small_fp64|lattice64] [--precision ...]
+                       [--workload dense4096|small_fp64|lattice64|ragged512]
+                       [--precision ...]
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own slice of replicas
 (replica_offset = rank * R, same seed): weak scaling, no collective in the timed region.
 """
@@ -274,6 +275,18 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "ragged512":
+        wl = Ragged()
+        cb = cpu_baseline_ragged(wl, budget_s=REF_BUDGET_S, steps=args.steps)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": wl.count * wl.R / cb["value"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl.label}, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     wl = Workload(args.workload, args.precision)
     o, R = _oracle(wl)
     o.run(min(max(args.warmup, 1), 2))
@@ -302,6 +315,164 @@ def reference_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------------- ragged batches
+class Ragged:
+    """512 dense SPD problems, N_k = 64 u with u uniform on {1..16}, lambda log-uniform
+    in [1, 1e2], Haar Q, f = x^-1/2 (one fitted GLE, s = 4), R = 32 replicas each,
+    BF16x3 force, FP32 state; tracked: the diagonal plus 32 seeded off-diagonal pairs
+    per problem; all problems stepped together by one problem pool (persistent force
+    kernel over (problem, 128-row block) items, chunks of steps replayed from a captured
+    CUDA graph, force configuration picked by the pool's autotuner)."""
+
+    name = "ragged512"
+    count, R, block, graph_steps = 512, 32, 1000, 50
+
+    def __init__(self):
+        from paper_1402_2095_gb300 import fit
+        self.seed = syn.BASE_SEED + 3
+        self.sizes = syn.ragged_sizes(self.count, seed=self.seed)
+        self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("inv_sqrt_1_100")
+        self.mats, self.pairs = [], []
+        for k, n in enumerate(self.sizes):
+            M, _, _ = syn.dense_spd(int(n), 1.0, 100.0, seed=self.seed * 1000 + k)
+            self.mats.append(M.astype(np.float32))
+            self.pairs.append(np.concatenate([syn.diag_pairs(int(n)),
+                                              syn.random_pairs(int(n), 32, seed=k)]))
+        self.label = ("512 dense SPD, N = 64u (u uniform 1..16), lambda log-uniform [1,1e2], "
+                      "f=x^-1/2, R=32 each, BF16x3 force, diagonal + 32 pairs each")
+        self.default_steps = 4000
+
+    def problem(self, k, seed_shift=0):
+        return dict(M=self.mats[k], a_p=self.a_p, c_p=self.c_p, dt=self.dt,
+                    seed=self.seed * 1000 + k + seed_shift, block=self.block,
+                    pairs=self.pairs[k])
+
+    def work(self, cls):
+        """Algorithmic bytes per launch of each pool kernel class (all HBM-bound):
+        force: M as BF16 hi+lo (4 B per element), q^T operand hi+lo in, M q out;
+        gle: 60 B per (i, r) (q, p, s1..s4, M q in; q, p, s1..s4, sample, operand out);
+        accumulate: the sample rows of every tracked pair."""
+        N = self.sizes.astype(np.float64)
+        R = self.R
+        if cls == "pool_force":
+            return float(np.sum(4.0 * N * N + 4.0 * N * R + 4.0 * N * R))
+        if cls == "pool_gle":
+            return float(np.sum(60.0 * N * R))
+        if cls == "pool_accum":
+            return float(sum(2 * 4 * R * len(p) for p in self.pairs))
+        return float("nan")
+
+
+def run_ragged(args, rank, world, local):
+    import torch
+    from paper_1402_2095_gb300 import Pool
+    wl = Ragged()
+    steps = args.steps if args.steps is not None else wl.default_steps
+    ws = 3 << 30
+    pool = Pool(ws, replicas=wl.R, precision="bf16x3", max_problems=wl.count,
+                graph_steps=wl.graph_steps)
+    for k in range(wl.count):
+        pool.add(**wl.problem(k), replica_offset=rank * wl.R)
+    pool.run(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(pool.stream)
+    pool.run(steps)
+    ev1.record(pool.stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = pool.stats()
+    prof = pool.profile(min(steps, 200))
+    peaks, peak_kind = _peaks()
+    name, (pms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_s = pms / cnt / 1e3
+    achieved = wl.work(name) / per_launch_s / 1e9
+    total = sum(v[0] for v in prof.values())
+    roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "peak_source": f"{peak_kind} copy", "frac": achieved / peaks["hbm_gbs"],
+            "kernel": name, "launch_us": per_launch_s * 1e6, "traffic": _traffic(name),
+            "share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
+    pool.close()
+    del pool
+    torch.cuda.synchronize()
+
+    # end to end through the public API: host matrices in, every problem's elements out
+    t0 = time.perf_counter()
+    g = Pool(ws, replicas=wl.R, precision="bf16x3", max_problems=wl.count,
+             graph_steps=wl.graph_steps)
+    hs = [g.add(**wl.problem(k, seed_shift=1), replica_offset=rank * wl.R)
+          for k in range(wl.count)]
+    g.run(steps)
+    for k, h in enumerate(hs):
+        g.elements(h, wl.pairs[k])
+    t_e2e = time.perf_counter() - t0
+    g.close()
+    h2d = sum(m.nbytes for m in wl.mats) + sum(p.nbytes for p in wl.pairs)
+    d2h = sum(len(p) * 3 * 8 for p in wl.pairs)
+
+    value = wl.count * wl.R * steps * world / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.label, "problems": wl.count, "sum_n": int(wl.sizes.sum()),
+                   "sum_n2": int(np.sum(wl.sizes.astype(np.int64) ** 2)),
+                   "replicas_per_problem": wl.R, "precision": "bf16x3",
+                   "graph_steps": wl.graph_steps, "tuned_variant": st["tuned_variant"],
+                   "tuned_grid": st["tuned_grid"], "tuned_force_us": st["tuned_us"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "per-step working set (M hi+lo %.0f MB + state) > L2; steps back to back"
+                         % (wl.work("pool_force") / 1e6)},
+        "gpu_launches": 3 * steps,
+        "clocks": clk,
+        "roofline": roof,
+        "e2e": {"value": wl.count * wl.R * steps * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_ragged(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_ragged(wl, budget_s=CPU_BUDGET_S, nsample=16, steps=None):
+    """The oracle on a seeded random sample of the 512 problems (R = 32 each, the same
+    tracked elements): replica-steps/s of the sample, an estimate for the whole mix."""
+    from oracle.fth import OracleFTH
+    pick = np.random.default_rng(wl.seed).choice(wl.count, size=nsample, replace=False)
+    done, t_used = 0, 0.0
+    per = budget_s / nsample
+    for k in pick:
+        kw = wl.problem(int(k))
+        o = OracleFTH(M=kw["M"].astype(np.float64), a_p=wl.a_p, c_p=wl.c_p, dt=wl.dt,
+                      replicas=wl.R, seed=kw["seed"], block=wl.block, pairs=kw["pairs"])
+        o.run(1)
+        n_steps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < per and (steps is None or n_steps < steps):
+            o.run(4)
+            n_steps += 4
+        t_used += time.perf_counter() - t0
+        done += n_steps * wl.R
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{wl.name}: {nsample} of {wl.count} problems (seeded), R={wl.R} each, "
+                      f"{done} replica-steps in {t_used:.1f} s"}
+
+
 # ---------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -310,7 +481,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense4096",
-                    choices=["dense4096", "small_fp64", "lattice64"])
+                    choices=["dense4096", "small_fp64", "lattice64", "ragged512"])
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -331,6 +502,11 @@ def main():
 
     from paper_1402_2095_gb300 import FTH, build
     build.build()
+    if args.workload == "ragged512":
+        rc = run_ragged(args, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     wl = Workload(args.workload, args.precision)
     steps = args.steps if args.steps is not None else wl.default_steps
     stream = torch.cuda.current_stream()

@@ -216,6 +216,97 @@ fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t ldm, float*
                                   const double* T, const double* S, double dt, uint64_t seed,
                                   uint32_t kappa, int mode, float* sample, void* stream);
 
+/* ----------------------------------------------------------------------------------
+ * Problem pools: many independent problems resident on one device and stepped together
+ * (ragged batches, continuous batching).  Problems of different order and kind (dense
+ * or CSR) share one set of launches per step: a persistent tensor-core force kernel
+ * over a work list of (problem, 128-row block) items for the dense ones, one
+ * element-wise GLE kernel, one fused CSR kernel, one accumulate/flush kernel with a CTA
+ * per problem.  Every launch reads its inputs from a device descriptor table, so a
+ * chunk of steps is replayed from a captured CUDA graph.  Problems are added and
+ * removed between runs; admission fails with FTH_E_WORKSPACE when the problem's
+ * footprint does not fit the free part of the pool's workspace.  A problem's noise
+ * (key = its seed, replicas from its replica_offset) and arithmetic do not depend on
+ * the other problems: its results are identical alone and in any mix.  Its first
+ * pool step is its prologue (start half only), as on a fresh fth_ctx.
+ * ---------------------------------------------------------------------------------- */
+typedef struct fth_pool fth_pool;
+
+typedef struct {
+    int64_t replicas;       /* R of every problem: 32, 64 or 128                          */
+    int precision;          /* dense force: FTH_PREC_BF16X3 or FTH_PREC_TF32 (CSR: FP32)   */
+    int64_t max_problems;   /* capacity of the problem table                              */
+    int64_t graph_steps;    /* steps per captured CUDA graph (0: direct launches)         */
+    void* stream;           /* cudaStream_t                                               */
+} fth_pool_options;
+
+typedef struct {
+    uint64_t seed;          /* Philox key of this problem                                 */
+    double dt;
+    int64_t burnin;         /* samples discarded                                          */
+    int64_t block;          /* samples per block                                          */
+    int observable;         /* enum fth_observable                                        */
+    const int64_t* pairs;   /* tracked elements (2 * npairs indices, host)                */
+    int64_t npairs;
+    int64_t replica_offset; /* global index of replica 0 in the noise counter              */
+} fth_problem_options;
+
+typedef struct {
+    int64_t live;           /* problems in the pool                                        */
+    size_t slab_bytes;      /* workspace available to problems                            */
+    size_t used_bytes;      /* of which allocated                                          */
+    int64_t force_items, gle_items, csr_items;
+    int tuned_variant;      /* force-kernel configuration chosen by the autotuner          */
+    int tuned_grid;
+    double tuned_us;        /* its measured time per force launch                          */
+    int64_t graphs;         /* CUDA graphs captured so far                                 */
+} fth_pool_stats_t;
+
+/* Create an empty pool on `workspace` (256-byte aligned device memory the caller owns
+ * for the pool's lifetime).  Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED, CUDA. */
+fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t bytes,
+                           fth_pool** out);
+
+/* Device bytes a problem would take in this pool (admission by footprint). */
+fth_status fth_pool_footprint(const fth_pool* pool, const fth_matrix* M, const fth_gle* gle,
+                              const fth_problem_options* po, size_t* bytes);
+
+/* Validate and add a problem (copies M, zero state); *handle identifies it.
+ * Errors: INVALID_ARG, NOT_SPD, UNSUPPORTED, WORKSPACE (does not fit: not admitted), CUDA. */
+fth_status fth_pool_add(fth_pool* pool, const fth_matrix* M, const fth_gle* gle,
+                        const fth_problem_options* po, int64_t* handle);
+
+/* Remove a problem and free its memory (between runs). */
+fth_status fth_pool_remove(fth_pool* pool, int64_t handle);
+
+/* Advance every problem by `steps` launches (asynchronous on the pool's stream). */
+fth_status fth_pool_run(fth_pool* pool, int64_t steps);
+
+/* As fth_elements, for one problem of the pool.  Synchronises the stream. */
+fth_status fth_pool_elements(fth_pool* pool, int64_t handle, const int64_t* pairs, int64_t k,
+                             double* values, double* errbars);
+
+/* Copy one state plane of a problem to host FP64, laid out as fth_get_state: q and p
+ * [R][n], s [R][s][n].  Synchronises the stream. */
+fth_status fth_pool_get_state(fth_pool* pool, int64_t handle, int plane, double* host);
+
+/* Counters of one problem (steps, samples, blocks ...).  Synchronises the stream. */
+fth_status fth_pool_problem_info(fth_pool* pool, int64_t handle, fth_info_t* info);
+
+fth_status fth_pool_stats(const fth_pool* pool, fth_pool_stats_t* stats);
+
+/* Kernel classes of a pool step, for fth_pool_profile. */
+enum fth_pool_kernel { FTH_PK_FORCE = 0, FTH_PK_GLE = 1, FTH_PK_CSR = 2, FTH_PK_ACCUM = 3,
+                       FTH_PK_CLASSES = 4 };
+
+/* Advance every problem by `steps` steps as direct launches with a CUDA event pair
+ * around each launch (on the pool's stream), and return per kernel class the summed
+ * device time in ms (`ms[FTH_PK_CLASSES]`) and the number of launches
+ * (`launches[FTH_PK_CLASSES]`, may be NULL).  The steps are real steps.  Synchronises. */
+fth_status fth_pool_profile(fth_pool* pool, int64_t steps, double* ms, int64_t* launches);
+const char* fth_pool_last_error(const fth_pool* pool);
+void fth_pool_destroy(fth_pool* pool);
+
 /* Library version string. */
 const char* fth_version(void);
 

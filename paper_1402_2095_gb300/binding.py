@@ -29,7 +29,10 @@ PLANE = {"q": 0, "p": 1, "s": 2}
 EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_get_state",
            "fth_set_state", "fth_info", "fth_status_poll", "fth_last_error", "fth_destroy",
            "fth_gle_propagator", "fth_version", "fth_profile_enable", "fth_profile_read",
-           "fth_dense_step_noalloc")
+           "fth_dense_step_noalloc", "fth_pool_create", "fth_pool_footprint", "fth_pool_add",
+           "fth_pool_remove", "fth_pool_run", "fth_pool_elements", "fth_pool_get_state",
+           "fth_pool_problem_info",
+           "fth_pool_stats", "fth_pool_profile", "fth_pool_last_error", "fth_pool_destroy")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense")
 
@@ -56,6 +59,26 @@ class fth_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("track", ctypes.c_int), ("pairs", ctypes.c_void_p),
                 ("npairs", ctypes.c_int64), ("stack", ctypes.c_int64), ("stream", ctypes.c_void_p),
                 ("replica_offset", ctypes.c_int64)]
+
+
+class fth_pool_options(ctypes.Structure):
+    _fields_ = [("replicas", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("max_problems", ctypes.c_int64), ("graph_steps", ctypes.c_int64),
+                ("stream", ctypes.c_void_p)]
+
+
+class fth_problem_options(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dt", ctypes.c_double), ("burnin", ctypes.c_int64),
+                ("block", ctypes.c_int64), ("observable", ctypes.c_int), ("pairs", ctypes.c_void_p),
+                ("npairs", ctypes.c_int64), ("replica_offset", ctypes.c_int64)]
+
+
+class fth_pool_stats_t(ctypes.Structure):
+    _fields_ = [("live", ctypes.c_int64), ("slab_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t), ("force_items", ctypes.c_int64),
+                ("gle_items", ctypes.c_int64), ("csr_items", ctypes.c_int64),
+                ("tuned_variant", ctypes.c_int), ("tuned_grid", ctypes.c_int),
+                ("tuned_us", ctypes.c_double), ("graphs", ctypes.c_int64)]
 
 
 class fth_info_t(ctypes.Structure):
@@ -96,6 +119,18 @@ def load(path: str = LIB_PATH):
         "fth_profile_read": ([P, P, P], INT),
         "fth_dense_step_noalloc": ([P, I64, I64, P, P, P, I64, I64, INT, P, P, D,
                                     ctypes.c_uint64, ctypes.c_uint32, INT, P, P], INT),
+        "fth_pool_create": ([P, P, ctypes.c_size_t, P], INT),
+        "fth_pool_footprint": ([P, P, P, P, P], INT),
+        "fth_pool_add": ([P, P, P, P, P], INT),
+        "fth_pool_remove": ([P, I64], INT),
+        "fth_pool_run": ([P, I64], INT),
+        "fth_pool_elements": ([P, I64, P, I64, P, P], INT),
+        "fth_pool_get_state": ([P, I64, INT, P], INT),
+        "fth_pool_problem_info": ([P, I64, P], INT),
+        "fth_pool_stats": ([P, P], INT),
+        "fth_pool_profile": ([P, I64, P, P], INT),
+        "fth_pool_last_error": ([P], ctypes.c_char_p),
+        "fth_pool_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -273,6 +308,179 @@ class FTH:
         if getattr(self, "ctx", None):
             load().fth_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------- problem pools
+def _matrix_struct(M=None, csr=None, keep=None):
+    import torch
+    mat = fth_matrix()
+    if M is not None:
+        mat.kind = DENSE
+        if isinstance(M, torch.Tensor):
+            t = M.contiguous()
+            if t.dtype not in (torch.float32, torch.float64):
+                t = t.float()
+            mat.dtype = F64 if t.dtype == torch.float64 else F32
+            mat.on_device = 1 if t.is_cuda else 0
+            mat.values = t.data_ptr()
+            mat.n = t.shape[0]
+            keep.append(t)
+        else:
+            a = np.ascontiguousarray(M)
+            if a.dtype not in (np.float32, np.float64):
+                a = a.astype(np.float64)
+            mat.dtype = F64 if a.dtype == np.float64 else F32
+            mat.values = a.ctypes.data
+            mat.n = a.shape[0]
+            keep.append(a)
+    else:
+        rowptr, col, val, n = csr
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        va = np.ascontiguousarray(val)
+        if va.dtype not in (np.float32, np.float64):
+            va = va.astype(np.float64)
+        mat.kind = CSR
+        mat.dtype = F64 if va.dtype == np.float64 else F32
+        mat.n = int(n)
+        mat.nnz = int(ci.size)
+        mat.values = va.ctypes.data
+        mat.rowptr = rp.ctypes.data
+        mat.colind = ci.ctypes.data
+        keep += [rp, ci, va]
+    return mat
+
+
+def _pool_check(status, pool):
+    if status != FTH_OK:
+        msg = load().fth_pool_last_error(pool)
+        raise FthError(status, msg.decode() if msg else "")
+
+
+class Pool:
+    """Many independent problems resident on the GPU, stepped together (ragged batches,
+    continuous batching).  `workspace_bytes` of device memory (a torch tensor) is the
+    admission capacity."""
+
+    def __init__(self, workspace_bytes, *, replicas=32, precision="bf16x3", max_problems=1024,
+                 graph_steps=0, stream=None):
+        import torch
+        L = load()
+        # a stream of its own by default: graphs cannot be captured on the legacy stream
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._aux = {}
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(int(workspace_bytes), dtype=torch.uint8, device="cuda")
+        o = fth_pool_options()
+        o.replicas = int(replicas)
+        o.precision = PRECISION[precision]
+        o.max_problems = int(max_problems)
+        o.graph_steps = int(graph_steps)
+        o.stream = self.stream.cuda_stream
+        self.replicas = int(replicas)
+        h = ctypes.c_void_p()
+        _check(L.fth_pool_create(ctypes.byref(o), self.workspace.data_ptr(), self.workspace.numel(),
+                                 ctypes.byref(h)))
+        self.pool = h
+
+    def _problem(self, M, csr, a_p, c_p, dt, seed, burnin, block, observable, pairs,
+                 replica_offset):
+        keep = []
+        mat = _matrix_struct(M, csr, keep)
+        gle = make_gle(a_p, c_p)
+        po = fth_problem_options()
+        po.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        po.dt = float(dt)
+        po.burnin = int(burnin)
+        po.block = int(block)
+        po.observable = OBSERVABLE[observable]
+        pr = np.ascontiguousarray(np.asarray(pairs if pairs is not None else np.zeros((0, 2)),
+                                             dtype=np.int64).reshape(-1, 2))
+        keep.append(pr)
+        po.pairs = pr.ctypes.data
+        po.npairs = pr.shape[0]
+        po.replica_offset = int(replica_offset)
+        return mat, gle, po, keep
+
+    def footprint(self, M=None, csr=None, *, a_p, c_p, dt, pairs=None, **kw):
+        mat, gle, po, keep = self._problem(M, csr, a_p, c_p, dt, 0, 0, 1, "p", pairs, 0)
+        b = ctypes.c_size_t(0)
+        _pool_check(load().fth_pool_footprint(self.pool, ctypes.byref(mat), ctypes.byref(gle),
+                                              ctypes.byref(po), ctypes.byref(b)), self.pool)
+        return int(b.value)
+
+    def add(self, M=None, csr=None, *, a_p, c_p, dt, seed=0, burnin=0, block=1000,
+            observable="p", pairs=None, replica_offset=0):
+        """Admit a problem; returns its handle.  Raises FthError(WORKSPACE) if it does
+        not fit."""
+        mat, gle, po, keep = self._problem(M, csr, a_p, c_p, dt, seed, burnin, block, observable,
+                                           pairs, replica_offset)
+        h = ctypes.c_int64(-1)
+        _pool_check(load().fth_pool_add(self.pool, ctypes.byref(mat), ctypes.byref(gle),
+                                        ctypes.byref(po), ctypes.byref(h)), self.pool)
+        self._aux[int(h.value)] = int(gle.s)
+        return int(h.value)
+
+    def remove(self, handle):
+        _pool_check(load().fth_pool_remove(self.pool, int(handle)), self.pool)
+        self._aux.pop(int(handle), None)
+
+    def run(self, steps):
+        _pool_check(load().fth_pool_run(self.pool, int(steps)), self.pool)
+
+    def elements(self, handle, pairs):
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        k = pr.shape[0]
+        vals = np.zeros(k)
+        errs = np.zeros(k)
+        _pool_check(load().fth_pool_elements(self.pool, int(handle), pr.ctypes.data, k,
+                                             vals.ctypes.data, errs.ctypes.data), self.pool)
+        return vals, errs
+
+    def get_state(self, handle, plane: str):
+        """State plane of one problem: q, p as (R, n); s as (R, s, n)."""
+        info = self.info(handle)
+        n = int(info["n"])
+        if plane == "s":
+            ns = self._aux[handle]
+            out = np.zeros((self.replicas, ns, n))
+        else:
+            out = np.zeros((self.replicas, n))
+        if out.size:
+            _pool_check(load().fth_pool_get_state(self.pool, int(handle), PLANE[plane],
+                                                  out.ctypes.data), self.pool)
+        return out
+
+    def info(self, handle) -> dict:
+        i = fth_info_t()
+        _pool_check(load().fth_pool_problem_info(self.pool, int(handle), ctypes.byref(i)), self.pool)
+        return {f: getattr(i, f) for f, _ in fth_info_t._fields_}
+
+    def stats(self) -> dict:
+        s = fth_pool_stats_t()
+        _check(load().fth_pool_stats(self.pool, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in fth_pool_stats_t._fields_}
+
+    POOL_KERNELS = ("pool_force", "pool_gle", "pool_csr", "pool_accum")
+
+    def profile(self, steps):
+        """Run `steps` real steps with each launch timed: {class: (total ms, launches)}."""
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int64)
+        _pool_check(load().fth_pool_profile(self.pool, int(steps), ms.ctypes.data, cnt.ctypes.data),
+                    self.pool)
+        return {k: (float(ms[c]), int(cnt[c])) for c, k in enumerate(self.POOL_KERNELS) if cnt[c]}
+
+    def close(self):
+        if getattr(self, "pool", None):
+            load().fth_pool_destroy(self.pool)
+            self.pool = None
 
     def __del__(self):
         try:

@@ -1,0 +1,67 @@
+// Problem-pool descriptors shared by the pool's host runtime and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fth_internal.h"
+
+namespace fth {
+
+// One problem slot, resident in device memory; the kernels read everything they need
+// from here (constants, buffers, counters), the accumulate kernel advances the counters.
+struct PoolDesc {
+    GleF32 g;               // D = T - I, S, dt, Philox keys (round keys), replica offset
+    int kind;               // 0 dense, 1 CSR
+    int n, np;              // order; dense: order padded to 128
+    int ns;                 // s + 1
+    int observable;
+    int npairs;
+    int live;
+    int pad0;
+    int64_t burnin, block;
+    // dense force operands: M blocked and pre-swizzled in 128-byte K slices
+    // ([n/128][np/KS][128][128 B]), q^T slices ([np/KS][R][128 B])
+    uint8_t* a_hi;
+    uint8_t* a_lo;
+    uint8_t* bt_hi;
+    uint8_t* bt_lo;
+    float* mq;              // M q, [n][R]
+    float* q[2];            // positions [n][R] (CSR: ping-pong, q[cur] current)
+    float* p;
+    float* s;               // ns - 1 planes of [n][R]
+    const int32_t* rowptr;  // CSR
+    const int32_t* col;
+    const float* val;
+    float* x;               // this step's sample [n][R]
+    const int32_t* pairs;   // 2 * npairs, local indices
+    float* partial;         // block partial sums
+    double* mean;           // Welford mean of the block means
+    double* m2;
+    // counters, advanced on the device by the accumulate kernel
+    int64_t t, nsamp, inblock, nblocks;
+    int primed, cur;
+};
+
+struct PoolForceItem {
+    int problem;
+    int rb;                 // 128-row block
+};
+
+struct PoolRowItem {
+    int problem;
+    int row0;               // first of 32 rows
+};
+
+cudaError_t launch_pool_force(int kind, int rn, int variant, const PoolDesc* desc,
+                              const PoolForceItem* items, int nitems, int grid, uint32_t* err,
+                              cudaStream_t st);
+int pool_force_max_ctas_per_sm(int kind, int rn, int variant);
+cudaError_t launch_pool_gle(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            int kind, cudaStream_t st);
+cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            cudaStream_t st);
+cudaError_t launch_pool_accum(PoolDesc* desc, const int* live, int nlive, int RN, uint32_t* err,
+                              cudaStream_t st);
+
+}  // namespace fth

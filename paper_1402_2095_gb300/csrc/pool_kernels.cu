@@ -1,0 +1,497 @@
+// Problem pools, device side: many independent problems resident on one GPU, stepped
+// together by work-list kernels whose every input comes from a device descriptor table,
+// so a whole chunk of steps can run from one captured CUDA graph.
+//
+// Per pool step (one fused launch of every problem, paper Eq. 2 / Eq. 5 / Eq. 6):
+//   pool_force_kernel   dense problems: MQ = M q over (problem, 128-row block) items, a
+//                       persistent tcgen05 kernel (tensor memory double-buffered so the
+//                       epilogue of one item overlaps the MMAs of the next).  M and the
+//                       q^T operand are stored pre-swizzled in 128-byte K slices, so plain
+//                       bulk copies land them in the SWIZZLE_128B layout the MMA reads;
+//   pool_gle_kernel     dense problems: the element-wise fused GLE step;
+//   pool_csr_kernel     CSR problems: fused SpMM + GLE step;
+//   pool_accum_kernel   one CTA per live problem: accumulate its tracked pairs for this
+//                       sample, advance its counters and flush its own completed blocks.
+// A problem's first launch is its prologue (start half only), exactly as a standalone
+// context; its noise (key = its seed) and arithmetic order do not depend on the other
+// problems in the pool, so its results are identical alone and in any mix.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "fth_internal.h"
+#include "gle_device.cuh"
+#include "pool_internal.h"
+#include "tc_primitives.cuh"
+
+namespace fth {
+using namespace tc;
+
+// ------------------------------------------------------------------ force work list
+template <int KIND, int RN, int STAGES>
+struct PoolCfg {
+    static constexpr int kOps = KIND == 1 ? 1 : 2;
+    static constexpr int kABytes = 128 * 128;          // 128 rows x one 128-byte K slice
+    static constexpr int kBBytes = RN * 128;
+    static constexpr int kStageBytes = kOps * (kABytes + kBBytes);
+    static constexpr int kTmemCols = (2 * RN) < 32 ? 32 : 2 * RN;   // two accumulators
+    static constexpr size_t kSmem = (size_t)STAGES * kStageBytes + 1024 + 8 * (2 * STAGES + 5) + 16;
+};
+
+// Warp roles: warp 0 lane 0 bulk copies, warp 1 lane 0 issues the MMAs, warps 2..5
+// (one per TMEM lane quadrant) drain the accumulators.  Items c, c + G, c + 2G ...
+template <int KIND, int RN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __restrict__ items,
+                  int nitems, uint32_t* err) {
+    using C = PoolCfg<KIND, RN, STAGES>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* stages = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(stages + STAGES * C::kStageBytes);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;     // [2] MMA -> epilogue
+    uint64_t* tempty = tfull + 2;         // [2] epilogue -> MMA
+    uint64_t* drain = tempty + 2;         // MMA completion after a timed-out wait
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(C::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    constexpr int KS = KIND == 1 ? 32 : 64;   // K elements per 128-byte slice
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int c = 0;
+        bool ok = true;
+        for (int j = blockIdx.x; j < nitems && ok; j += gridDim.x) {
+            const PoolForceItem it = items[j];
+            const PoolDesc& d = desc[it.problem];
+            const int nk = d.np / KS;
+            const uint8_t* a_hi = d.a_hi + (size_t)it.rb * nk * C::kABytes;
+            const uint8_t* a_lo = d.a_lo + (size_t)it.rb * nk * C::kABytes;
+            for (int kb = 0; kb < nk && ok; ++kb, ++c) {
+                const int st = c % STAGES;
+                if (c >= STAGES) ok = mbar_wait(&empty[st], ((c / STAGES) + 1) & 1, err);
+                if (!ok) break;
+                uint8_t* base = stages + st * C::kStageBytes;
+                mbar_expect_tx(&full[st], C::kStageBytes);
+                bulk_load(base, a_hi + (size_t)kb * C::kABytes, C::kABytes, &full[st]);
+                bulk_load(base + C::kABytes, d.bt_hi + (size_t)kb * C::kBBytes, C::kBBytes, &full[st]);
+                if (KIND == 2) {
+                    bulk_load(base + C::kABytes + C::kBBytes, a_lo + (size_t)kb * C::kABytes,
+                              C::kABytes, &full[st]);
+                    bulk_load(base + 2 * C::kABytes + C::kBBytes, d.bt_lo + (size_t)kb * C::kBBytes,
+                              C::kBBytes, &full[st]);
+                }
+            }
+        }
+        if (!ok) {
+            for (int k = std::max(0, c - STAGES); k < c; ++k)
+                mbar_wait(&full[k % STAGES], (k / STAGES) & 1, err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = (1u << 4) | ((uint32_t)(KIND == 1 ? 2 : 1) << 7) |
+                                   ((uint32_t)(KIND == 1 ? 2 : 1) << 10) |
+                                   ((uint32_t)(RN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        int c = 0, u = 0;
+        bool ok = true;
+        for (int j = blockIdx.x; j < nitems && ok; j += gridDim.x, ++u) {
+            const int a = u & 1;
+            if (u >= 2) ok = mbar_wait(&tempty[a], ((u >> 1) - 1) & 1, err);
+            if (!ok) break;
+            fence_after_sync();
+            const PoolForceItem it = items[j];
+            const int nk = desc[it.problem].np / KS;
+            const uint32_t acc_t = tmem + (uint32_t)(a * RN);
+            for (int kb = 0; kb < nk; ++kb, ++c) {
+                const int st = c % STAGES;
+                if (!mbar_wait(&full[st], (c / STAGES) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t base = smem_u32(stages + st * C::kStageBytes);
+                const uint64_t ah = sw128_desc(base);
+                const uint64_t bh = sw128_desc(base + C::kABytes);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    if (KIND == 1) {
+                        umma<1>(acc_t, ah + adv, bh + adv, idesc, acc);
+                    } else {
+                        const uint64_t al = sw128_desc(base + C::kABytes + C::kBBytes);
+                        const uint64_t bl = sw128_desc(base + 2 * C::kABytes + C::kBBytes);
+                        umma<2>(acc_t, al + adv, bh + adv, idesc, acc);
+                        umma<2>(acc_t, ah + adv, bl + adv, idesc, 1u);
+                        umma<2>(acc_t, ah + adv, bh + adv, idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[st]);
+            }
+            umma_commit(&tfull[a]);
+        }
+        if (!ok) {
+            // let every MMA issued so far finish before the tensor memory is freed
+            atomicOr(err, kErrTimeout);
+            umma_commit(drain);
+            mbar_wait(drain, 0, err);
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp & 3;
+        int u = 0;
+        for (int j = blockIdx.x; j < nitems; j += gridDim.x, ++u) {
+            const int a = u & 1;
+            // warp-uniform: tcgen05.ld below is .sync.aligned
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[a], (u >> 1) & 1, err));
+            fence_after_sync();
+            const PoolForceItem it = items[j];
+            const PoolDesc& d = desc[it.problem];
+            const int row = it.rb * 128 + q * 32 + lane;
+            float* dst = d.mq + (size_t)row * RN;
+#pragma unroll 1
+            for (int c16 = 0; c16 < RN / 16; ++c16) {
+                float v[16];
+                if (ok) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * RN + c16 * 16), v);
+                if (ok && row < d.n) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj += 4)
+                        *reinterpret_cast<float4*>(dst + c16 * 16 + jj) =
+                            make_float4(v[jj], v[jj + 1], v[jj + 2], v[jj + 3]);
+                }
+            }
+            fence_before_sync();
+            mbar_arrive(&tempty[a]);
+            if (!ok) break;
+        }
+    }
+    __syncwarp();
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(C::kTmemCols));
+    }
+}
+
+template <int KIND, int RN, int STAGES>
+cudaError_t launch_pool_force_t(const PoolDesc* desc, const PoolForceItem* items, int nitems,
+                                int grid, uint32_t* err, cudaStream_t st) {
+    using C = PoolCfg<KIND, RN, STAGES>;
+    static_assert(C::kSmem <= 232448, "shared memory");
+    auto kern = pool_force_kernel<KIND, RN, STAGES>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+    kern<<<grid, 192, C::kSmem, st>>>(desc, items, nitems, err);
+    return cudaGetLastError();
+}
+
+// Stage counts: "deep" fills ~200 KB of shared memory (one CTA per SM), "shallow" fits
+// two CTAs per SM.
+template <int KIND, int RN>
+struct PoolStages {
+    static constexpr int kStage = PoolCfg<KIND, RN, 1>::kStageBytes;
+    static constexpr int kDeep = (200 * 1024) / kStage < 8 ? (200 * 1024) / kStage : 8;
+    static constexpr int kShallow = (100 * 1024) / kStage < 4 ? (100 * 1024) / kStage : 4;
+};
+
+template <int KIND, int RN>
+cudaError_t pool_force_rn(int variant, const PoolDesc* desc, const PoolForceItem* items,
+                          int nitems, int grid, uint32_t* err, cudaStream_t st) {
+    using S = PoolStages<KIND, RN>;
+    if (variant == 0 || S::kShallow < 2)
+        return launch_pool_force_t<KIND, RN, S::kDeep>(desc, items, nitems, grid, err, st);
+    return launch_pool_force_t<KIND, RN, (S::kShallow < 2 ? 2 : S::kShallow)>(desc, items, nitems,
+                                                                              grid, err, st);
+}
+
+cudaError_t launch_pool_force(int kind, int rn, int variant, const PoolDesc* desc,
+                              const PoolForceItem* items, int nitems, int grid, uint32_t* err,
+                              cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+#define FTH_POOL_RN(KV, RV) \
+    if (kind == KV && rn == RV) return pool_force_rn<KV, RV>(variant, desc, items, nitems, grid, err, st);
+    FTH_POOL_RN(1, 32)
+    FTH_POOL_RN(1, 64)
+    FTH_POOL_RN(1, 128)
+    FTH_POOL_RN(2, 32)
+    FTH_POOL_RN(2, 64)
+    FTH_POOL_RN(2, 128)
+#undef FTH_POOL_RN
+    return cudaErrorInvalidValue;
+}
+
+int pool_force_max_ctas_per_sm(int kind, int rn, int variant) {
+    (void)kind;
+    (void)rn;
+    return variant == 0 ? 1 : 2;
+}
+
+// ------------------------------------------------------------------ element-wise dense step
+// q^T operand in the pre-swizzled slice layout the force kernel copies:
+// slice kb = i / KS holds RN rows of 128 bytes; 16-byte chunk c of row r sits at
+// chunk position c ^ (r & 7).
+__device__ __forceinline__ size_t swz_offset(int r, int i, int KS, int esz, int RN) {
+    const int kb = i / KS;
+    const int col = (i % KS) * esz;
+    return (size_t)kb * RN * 128 + (size_t)r * 128 + (size_t)((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+}
+
+__device__ __forceinline__ float to_tf32_pool(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int NS>
+__device__ __forceinline__ void pool_gle_rows(const PoolDesc& d, int i, int r0, int RN, int kind) {
+    const size_t plane = (size_t)d.n * RN;
+    const size_t off = (size_t)i * RN + r0;
+    const float4 mq4 = *reinterpret_cast<const float4*>(d.mq + off);
+    float* q = d.q[0];
+    float4 q4 = *reinterpret_cast<const float4*>(q + off);
+    float4 v4[NS];
+    v4[0] = *reinterpret_cast<const float4*>(d.p + off);
+#pragma unroll
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(d.s + (a - 1) * plane + off);
+    const int flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
+    const uint32_t kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+    float* qa = reinterpret_cast<float*>(&q4);
+    const float* mqa = reinterpret_cast<const float*>(&mq4);
+    float samp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float v[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+        float xi[2 * NS];
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + d.g.roff, d.g.rk, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], d.g, xi, flags, d.observable, samp[e]);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+    }
+    *reinterpret_cast<float4*>(q + off) = q4;
+    *reinterpret_cast<float4*>(d.p + off) = v4[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(d.s + (a - 1) * plane + off) = v4[a];
+    if (d.primed)
+        *reinterpret_cast<float4*>(d.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
+    // force operand for the next step
+    if (kind == 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float*>(d.bt_hi + swz_offset(r0 + e, i, 32, 4, RN)) = to_tf32_pool(qa[e]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(qa[e]);
+            const size_t o = swz_offset(r0 + e, i, 64, 2, RN);
+            *reinterpret_cast<__nv_bfloat16*>(d.bt_hi + o) = hb;
+            *reinterpret_cast<__nv_bfloat16*>(d.bt_lo + o) =
+                __float2bfloat16_rn(qa[e] - __bfloat162float(hb));
+        }
+    }
+}
+
+// blockDim (32, 8): item = 32 rows of one problem; the 8 y-threads cover 32 replicas per
+// pass (4 each) and loop over the RN / 32 replica chunks.
+__global__ void __launch_bounds__(256, 2)
+pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
+                int nitems, int RN, int kind) {
+    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
+        const PoolRowItem it = items[j];
+        const PoolDesc& d = desc[it.problem];
+        const int i = it.row0 + threadIdx.x;
+        if (i >= d.n) continue;
+        for (int r0 = threadIdx.y * 4; r0 < RN; r0 += 32) {
+            switch (d.ns) {
+                case 1: pool_gle_rows<1>(d, i, r0, RN, kind); break;
+                case 2: pool_gle_rows<2>(d, i, r0, RN, kind); break;
+                case 3: pool_gle_rows<3>(d, i, r0, RN, kind); break;
+                case 4: pool_gle_rows<4>(d, i, r0, RN, kind); break;
+                default: pool_gle_rows<5>(d, i, r0, RN, kind); break;
+            }
+        }
+    }
+}
+
+cudaError_t launch_pool_gle(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            int kind, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = std::min(nitems, 152 * 12);
+    pool_gle_kernel<<<grid, dim3(32, 8), 0, st>>>(desc, items, nitems, RN, kind);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CSR fused step
+template <int NS>
+__device__ __forceinline__ void pool_csr_rows(const PoolDesc& d, int i, int r0, int RN) {
+    const size_t plane = (size_t)d.n * RN;
+    const size_t off = (size_t)i * RN + r0;
+    const float* qin = d.q[d.cur];
+    float* qout = d.q[d.cur ^ 1];
+    float4 mq4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e1 = d.rowptr[i + 1];
+    for (int e = d.rowptr[i]; e < e1; ++e) {
+        const float m = d.val[e];
+        const float4 x = *reinterpret_cast<const float4*>(qin + (size_t)d.col[e] * RN + r0);
+        mq4.x = fmaf(m, x.x, mq4.x);
+        mq4.y = fmaf(m, x.y, mq4.y);
+        mq4.z = fmaf(m, x.z, mq4.z);
+        mq4.w = fmaf(m, x.w, mq4.w);
+    }
+    float4 q4 = *reinterpret_cast<const float4*>(qin + off);
+    float4 v4[NS];
+    v4[0] = *reinterpret_cast<const float4*>(d.p + off);
+#pragma unroll
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(d.s + (a - 1) * plane + off);
+    const int flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
+    const uint32_t kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+    float* qa = reinterpret_cast<float*>(&q4);
+    const float* mqa = reinterpret_cast<const float*>(&mq4);
+    float samp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float v[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+        float xi[2 * NS];
+        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + d.g.roff, d.g.rk, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], d.g, xi, flags, d.observable, samp[e]);
+#pragma unroll
+        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+    }
+    *reinterpret_cast<float4*>(qout + off) = q4;
+    *reinterpret_cast<float4*>(d.p + off) = v4[0];
+#pragma unroll
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(d.s + (a - 1) * plane + off) = v4[a];
+    if (d.primed)
+        *reinterpret_cast<float4*>(d.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
+}
+
+__global__ void __launch_bounds__(256, 2)
+pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
+                int nitems, int RN) {
+    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
+        const PoolRowItem it = items[j];
+        const PoolDesc& d = desc[it.problem];
+        const int i = it.row0 + threadIdx.x;
+        if (i >= d.n) continue;
+        for (int r0 = threadIdx.y * 4; r0 < RN; r0 += 32) {
+            switch (d.ns) {
+                case 1: pool_csr_rows<1>(d, i, r0, RN); break;
+                case 2: pool_csr_rows<2>(d, i, r0, RN); break;
+                case 3: pool_csr_rows<3>(d, i, r0, RN); break;
+                case 4: pool_csr_rows<4>(d, i, r0, RN); break;
+                default: pool_csr_rows<5>(d, i, r0, RN); break;
+            }
+        }
+    }
+}
+
+cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = std::min(nitems, 152 * 12);
+    pool_csr_kernel<<<grid, dim3(32, 8), 0, st>>>(desc, items, nitems, RN);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ accumulate, advance, flush
+// One CTA per live problem.  A prologue launch only marks the problem primed.
+__global__ void __launch_bounds__(256)
+pool_accum_kernel(PoolDesc* __restrict__ desc, const int* __restrict__ live, int nlive, int RN,
+                  uint32_t* err) {
+    __shared__ int s_take, s_flush;
+    __shared__ double s_nb;
+    for (int j = blockIdx.x; j < nlive; j += gridDim.x) {
+        PoolDesc& d = desc[live[j]];
+        if (threadIdx.x == 0) {
+            s_take = d.primed && d.nsamp >= d.burnin;
+            s_flush = 0;
+        }
+        __syncthreads();
+        if (d.primed && s_take) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int e = warp; e < d.npairs; e += blockDim.x >> 5) {
+                const float* a = d.x + (size_t)d.pairs[2 * e] * RN;
+                const float* b = d.x + (size_t)d.pairs[2 * e + 1] * RN;
+                float acc = 0.f;
+                for (int r = lane; r < RN; r += 32) acc = fmaf(a[r], b[r], acc);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) d.partial[e] += acc;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!d.primed) {
+                d.primed = 1;
+            } else {
+                d.t += 1;
+                d.nsamp += 1;
+                if (s_take) {
+                    d.inblock += 1;
+                    if (d.inblock == d.block) {
+                        s_flush = 1;
+                        s_nb = (double)(d.nblocks + 1);
+                    }
+                }
+            }
+            if (d.kind == 1) d.cur ^= 1;
+        }
+        __syncthreads();
+        if (s_flush) {
+            const double inv = 1.0 / ((double)d.block * (double)RN);
+            bool bad = false;
+            for (int e = threadIdx.x; e < d.npairs; e += blockDim.x) {
+                const double bm = (double)d.partial[e] * inv;
+                bad |= !isfinite(bm);
+                const double dl = bm - d.mean[e];
+                const double mu = d.mean[e] + dl / s_nb;
+                d.m2[e] += dl * (bm - mu);
+                d.mean[e] = mu;
+                d.partial[e] = 0.f;
+            }
+            if (bad) atomicOr(err, kErrNonFinite);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                d.nblocks += 1;
+                d.inblock = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pool_accum(PoolDesc* desc, const int* live, int nlive, int RN, uint32_t* err,
+                              cudaStream_t st) {
+    if (nlive <= 0) return cudaSuccess;
+    pool_accum_kernel<<<std::min(nlive, 152 * 8), 256, 0, st>>>(desc, live, nlive, RN, err);
+    return cudaGetLastError();
+}
+
+}  // namespace fth
