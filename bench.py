@@ -165,6 +165,12 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # nvidia-smi's first query initialises NVML; let that finish before timing starts
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 10.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -433,6 +439,7 @@ def run_ragged(args, rank, world, local):
                    "replicas_per_problem": wl.R, "precision": "bf16x3",
                    "graph_steps": wl.graph_steps, "tuned_variant": st["tuned_variant"],
                    "tuned_grid": st["tuned_grid"], "tuned_force_us": st["tuned_us"],
+                   "gle_variant": st["gle_variant"], "tuned_gle_us": st["gle_us"],
                    "parallelism": f"replicas x{world}",
                    "l2": "per-step working set (M hi+lo %.0f MB + state) > L2; steps back to back"
                          % (wl.work("pool_force") / 1e6)},

@@ -259,6 +259,8 @@ typedef struct {
     int tuned_variant;      /* force-kernel configuration chosen by the autotuner          */
     int tuned_grid;
     double tuned_us;        /* its measured time per force launch                          */
+    int gle_variant;        /* dense GLE kernel configuration chosen by the autotuner      */
+    double gle_us;          /* its measured time per launch                                */
     int64_t graphs;         /* CUDA graphs captured so far                                 */
 } fth_pool_stats_t;
 

@@ -78,7 +78,8 @@ class fth_pool_stats_t(ctypes.Structure):
                 ("used_bytes", ctypes.c_size_t), ("force_items", ctypes.c_int64),
                 ("gle_items", ctypes.c_int64), ("csr_items", ctypes.c_int64),
                 ("tuned_variant", ctypes.c_int), ("tuned_grid", ctypes.c_int),
-                ("tuned_us", ctypes.c_double), ("graphs", ctypes.c_int64)]
+                ("tuned_us", ctypes.c_double), ("gle_variant", ctypes.c_int),
+                ("gle_us", ctypes.c_double), ("graphs", ctypes.c_int64)]
 
 
 class fth_info_t(ctypes.Structure):

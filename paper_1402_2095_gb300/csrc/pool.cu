@@ -124,15 +124,16 @@ struct fth_pool {
     PoolDesc* d_desc = nullptr;
     PoolForceItem* d_force = nullptr;
     PoolRowItem* d_rows = nullptr;     // dense rows, then CSR rows
-    int* d_live = nullptr;
+    PoolAccItem* d_acc = nullptr;
     uint32_t* d_err = nullptr;
-    int64_t cap_force = 0, cap_rows = 0;
+    int64_t cap_force = 0, cap_rows = 0, cap_acc = 0;
     size_t slab_begin = 0, slab_end = 0;
     std::map<size_t, size_t> free_list;   // offset -> bytes
     size_t used_bytes = 0;
     std::vector<Problem> probs;
     std::vector<PoolForceItem> h_force;
     std::vector<PoolRowItem> h_rows;
+    std::vector<PoolAccItem> h_acc;
     std::vector<int> h_live;
     int64_t n_force = 0, n_dense_rows = 0, n_csr_rows = 0;
     bool dirty = true;
@@ -140,6 +141,9 @@ struct fth_pool {
     int variant = 0, grid = 152;
     int64_t tuned_items = 0;   // force-list length the tuning was done on
     double tuned_us = 0.0;
+    int gle_variant = 1;
+    bool gle_tuned = false;
+    double gle_us = 0.0;
     int sms = 152;
     cudaGraphExec_t gexec = nullptr;
     bool graph_valid = false;
@@ -215,12 +219,17 @@ fth_status rebuild_lists(fth_pool* P) {
     P->h_force.clear();
     P->h_rows.clear();
     P->h_live.clear();
+    P->h_acc.clear();
     std::vector<PoolRowItem> csr_rows;
     for (int b = 0; b < (int)P->probs.size(); ++b) {
         const Problem& pr = P->probs[b];
         if (!pr.used) continue;
         P->h_live.push_back(b);
         const int n = pr.h.n;
+        const int np = (int)pr.npairs;
+        const int nch = std::max(1, (np + kPoolAccChunk - 1) / kPoolAccChunk);
+        for (int c = 0; c < nch; ++c)
+            P->h_acc.push_back({b, c * kPoolAccChunk, std::min(np, (c + 1) * kPoolAccChunk), nch});
         if (pr.h.kind == 0) {
             for (int rb = 0; rb < (n + 127) / 128; ++rb) P->h_force.push_back({b, rb});
             for (int r0 = 0; r0 < n; r0 += 32) P->h_rows.push_back({b, r0});
@@ -237,7 +246,8 @@ fth_status rebuild_lists(fth_pool* P) {
     P->n_dense_rows = (int64_t)P->h_rows.size();
     P->n_csr_rows = (int64_t)csr_rows.size();
     P->h_rows.insert(P->h_rows.end(), csr_rows.begin(), csr_rows.end());
-    if (P->n_force > P->cap_force || (int64_t)P->h_rows.size() > P->cap_rows)
+    if (P->n_force > P->cap_force || (int64_t)P->h_rows.size() > P->cap_rows ||
+        (int64_t)P->h_acc.size() > P->cap_acc)
         return perr(P, FTH_E_WORKSPACE, "work lists exceed the pool's capacity");
     if (!P->h_force.empty())
         PCK(cudaMemcpyAsync(P->d_force, P->h_force.data(), P->h_force.size() * sizeof(PoolForceItem),
@@ -245,9 +255,9 @@ fth_status rebuild_lists(fth_pool* P) {
     if (!P->h_rows.empty())
         PCK(cudaMemcpyAsync(P->d_rows, P->h_rows.data(), P->h_rows.size() * sizeof(PoolRowItem),
                             cudaMemcpyHostToDevice, P->stream), "h2d row items");
-    if (!P->h_live.empty())
-        PCK(cudaMemcpyAsync(P->d_live, P->h_live.data(), P->h_live.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, P->stream), "h2d live list");
+    if (!P->h_acc.empty())
+        PCK(cudaMemcpyAsync(P->d_acc, P->h_acc.data(), P->h_acc.size() * sizeof(PoolAccItem),
+                            cudaMemcpyHostToDevice, P->stream), "h2d accumulate items");
     PCK(cudaStreamSynchronize(P->stream), "sync");
     P->dirty = false;
     P->graph_valid = false;
@@ -268,8 +278,8 @@ fth_status enqueue_step(fth_pool* P, cudaEvent_t* ev = nullptr) {
     }
     if (P->n_dense_rows > 0) {
         PCK(mark(FTH_PK_GLE, 0), "event");
-        PCK(launch_pool_gle(P->d_desc, P->d_rows, (int)P->n_dense_rows, (int)P->R, P->kind_tc,
-                            P->stream), "pool gle");
+        PCK(launch_pool_gle(P->gle_variant, P->d_desc, P->d_rows, (int)P->n_dense_rows,
+                            (int)P->R, P->kind_tc, P->stream), "pool gle");
         PCK(mark(FTH_PK_GLE, 1), "event");
     }
     if (P->n_csr_rows > 0) {
@@ -279,7 +289,7 @@ fth_status enqueue_step(fth_pool* P, cudaEvent_t* ev = nullptr) {
         PCK(mark(FTH_PK_CSR, 1), "event");
     }
     PCK(mark(FTH_PK_ACCUM, 0), "event");
-    PCK(launch_pool_accum(P->d_desc, P->d_live, (int)P->h_live.size(), (int)P->R, P->d_err,
+    PCK(launch_pool_accum(P->d_desc, P->d_acc, (int)P->h_acc.size(), (int)P->R, P->d_err,
                           P->stream), "pool accumulate");
     PCK(mark(FTH_PK_ACCUM, 1), "event");
     return FTH_OK;
@@ -327,6 +337,42 @@ fth_status autotune(fth_pool* P) {
     return FTH_OK;
 }
 
+// The dense GLE kernel's variants differ only in how lanes map onto elements, so they
+// give identical results: time each on real steps (kGleReps steps apiece, the fastest
+// launch counts) and keep the fastest.  These steps are part of the run that asked.
+constexpr int kGleReps = 3;
+constexpr int64_t kGleTuneSteps = (int64_t)kPoolGleVariants * kGleReps;
+
+fth_status autotune_gle(fth_pool* P) {
+    cudaEvent_t ev[2 * FTH_PK_CLASSES];
+    for (auto& e : ev) PCK(cudaEventCreate(&e), "event");
+    double best = 1e30;
+    int pick = P->gle_variant;
+    fth_status st = FTH_OK;
+    for (int v = 0; v < kPoolGleVariants && st == FTH_OK; ++v) {
+        P->gle_variant = v;
+        double vbest = 1e30;
+        for (int k = 0; k < kGleReps && st == FTH_OK; ++k) {
+            st = enqueue_step(P, ev);
+            if (st == FTH_OK && cudaStreamSynchronize(P->stream) != cudaSuccess)
+                st = perr(P, FTH_E_CUDA, "sync");
+            float ms = 0.f;
+            if (st == FTH_OK) cudaEventElapsedTime(&ms, ev[2 * FTH_PK_GLE], ev[2 * FTH_PK_GLE + 1]);
+            vbest = std::min(vbest, (double)ms * 1e3);
+        }
+        if (vbest < best) {
+            best = vbest;
+            pick = v;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    P->gle_variant = pick;
+    P->gle_us = best;
+    P->gle_tuned = true;
+    P->graph_valid = false;
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -357,6 +403,8 @@ fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t 
     const size_t min_problem = a256((size_t)32 * P->R * 4);
     P->cap_force = (int64_t)(bytes / 65536) + P->max_problems;
     P->cap_rows = (int64_t)(bytes / (min_problem * 4)) + P->max_problems;
+    // a tracked pair takes >= 28 bytes of a problem's slab (indices, partial, mean, M2)
+    P->cap_acc = (int64_t)(bytes / (28 * (size_t)kPoolAccChunk)) + P->max_problems;
     size_t o = 0;
     const size_t off_desc = o;
     o = a256(o + sizeof(PoolDesc) * (size_t)P->max_problems);
@@ -364,8 +412,8 @@ fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t 
     o = a256(o + sizeof(PoolForceItem) * (size_t)P->cap_force);
     const size_t off_rows = o;
     o = a256(o + sizeof(PoolRowItem) * (size_t)P->cap_rows);
-    const size_t off_live = o;
-    o = a256(o + sizeof(int) * (size_t)P->max_problems);
+    const size_t off_acc = o;
+    o = a256(o + sizeof(PoolAccItem) * (size_t)P->cap_acc);
     const size_t off_err = o;
     o = a256(o + 256);
     if (o >= bytes) {
@@ -375,7 +423,7 @@ fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t 
     P->d_desc = reinterpret_cast<PoolDesc*>(P->ws + off_desc);
     P->d_force = reinterpret_cast<PoolForceItem*>(P->ws + off_force);
     P->d_rows = reinterpret_cast<PoolRowItem*>(P->ws + off_rows);
-    P->d_live = reinterpret_cast<int*>(P->ws + off_live);
+    P->d_acc = reinterpret_cast<PoolAccItem*>(P->ws + off_acc);
     P->d_err = reinterpret_cast<uint32_t*>(P->ws + off_err);
     P->slab_begin = o;
     P->slab_end = bytes & ~size_t(255);
@@ -601,7 +649,12 @@ fth_status fth_pool_run(fth_pool* P, int64_t steps) {
         if (st != FTH_OK) return st;
     }
     int64_t done = 0;
-    if (P->graph_steps > 0 && steps >= P->graph_steps) {
+    if (!P->gle_tuned && P->n_dense_rows > 0 && steps >= kGleTuneSteps) {
+        const fth_status st = autotune_gle(P);
+        if (st != FTH_OK) return st;
+        done = kGleTuneSteps;
+    }
+    if (P->graph_steps > 0 && steps - done >= P->graph_steps) {
         if (!P->graph_valid) {
             if (P->gexec) {
                 cudaGraphExecDestroy(P->gexec);
@@ -744,6 +797,8 @@ fth_status fth_pool_stats(const fth_pool* P, fth_pool_stats_t* s) {
     s->tuned_variant = P->variant;
     s->tuned_grid = P->grid;
     s->tuned_us = P->tuned_us;
+    s->gle_variant = P->gle_variant;
+    s->gle_us = P->gle_us;
     s->graphs = P->graphs;
     return FTH_OK;
 }

@@ -41,6 +41,8 @@ struct PoolDesc {
     // counters, advanced on the device by the accumulate kernel
     int64_t t, nsamp, inblock, nblocks;
     int primed, cur;
+    int done;               // accumulate items of this step finished (reset by the last)
+    int pad1;
 };
 
 struct PoolForceItem {
@@ -53,15 +55,24 @@ struct PoolRowItem {
     int row0;               // first of 32 rows
 };
 
+// Accumulate work: pairs [e0, e1) of one problem; the problem has `nchunks` items.
+struct PoolAccItem {
+    int problem;
+    int e0, e1;
+    int nchunks;
+};
+constexpr int kPoolAccChunk = 256;   // pairs per item (one thread each)
+
 cudaError_t launch_pool_force(int kind, int rn, int variant, const PoolDesc* desc,
                               const PoolForceItem* items, int nitems, int grid, uint32_t* err,
                               cudaStream_t st);
 int pool_force_max_ctas_per_sm(int kind, int rn, int variant);
-cudaError_t launch_pool_gle(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
-                            int kind, cudaStream_t st);
+constexpr int kPoolGleVariants = 3;
+cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
+                            int nitems, int RN, int kind, cudaStream_t st);
 cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
                             cudaStream_t st);
-cudaError_t launch_pool_accum(PoolDesc* desc, const int* live, int nlive, int RN, uint32_t* err,
-                              cudaStream_t st);
+cudaError_t launch_pool_accum(PoolDesc* desc, const PoolAccItem* items, int nitems, int RN,
+                              uint32_t* err, cudaStream_t st);
 
 }  // namespace fth

@@ -107,7 +107,7 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
             }
         }
         if (!ok) {
-            for (int k = std::max(0, c - STAGES); k < c; ++k)
+            for (int k = c > STAGES ? c - STAGES : 0; k < c; ++k)
                 mbar_wait(&full[k % STAGES], (k / STAGES) & 1, err);
         }
     } else if (warp == 1 && lane == 0) {
@@ -251,14 +251,16 @@ int pool_force_max_ctas_per_sm(int kind, int rn, int variant) {
 }
 
 // ------------------------------------------------------------------ element-wise dense step
-// q^T operand in the pre-swizzled slice layout the force kernel copies:
-// slice kb = i / KS holds RN rows of 128 bytes; 16-byte chunk c of row r sits at
-// chunk position c ^ (r & 7).
-__device__ __forceinline__ size_t swz_offset(int r, int i, int KS, int esz, int RN) {
-    const int kb = i / KS;
-    const int col = (i % KS) * esz;
-    return (size_t)kb * RN * 128 + (size_t)r * 128 + (size_t)((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
-}
+// Warp tasks: task = (32-row item, sub-block of 4 rows).  In each 32-replica pass a
+// row is covered by 32 / NE lanes of NE consecutive replicas each, so every state load
+// and store of a warp is whole 128-byte row segments.
+// Warps are independent (no block barrier): each stages its problem's GLE constants in
+// its own shared-memory slot, and transposes its new positions through a 4 x 32 slot
+// to write the next force operand, q^T in the pre-swizzled slice layout the force
+// kernel copies (slice kb = i / KS of RN rows x 128 bytes, 16-byte chunk c of row r at
+// position c ^ (r & 7)): lane r writes replica r's 4 rows (TF32: 16 bytes; BF16: 8
+// bytes of hi and 8 of lo).
+constexpr int kPoolMaxRN = 128;
 
 __device__ __forceinline__ float to_tf32_pool(float x) {
     uint32_t r;
@@ -266,84 +268,179 @@ __device__ __forceinline__ float to_tf32_pool(float x) {
     return __uint_as_float(r);
 }
 
-template <int NS>
-__device__ __forceinline__ void pool_gle_rows(const PoolDesc& d, int i, int r0, int RN, int kind) {
-    const size_t plane = (size_t)d.n * RN;
+struct PoolGleShared {
+    GleF32 g;
+    float* q;
+    float* p;
+    float* s;
+    float* mq;
+    float* x;
+    uint8_t* bt_hi;
+    uint8_t* bt_lo;
+    int n, ns, flags, observable, primed;
+    uint32_t kappa;
+};
+
+template <int NE> struct VecF;
+template <> struct VecF<2> { using T = float2; };
+template <> struct VecF<4> { using T = float4; };
+
+// NE consecutive replicas r0 .. r0 + NE - 1 of row i.
+template <int NS, int NE>
+__device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, int i, int r0, int RN,
+                                             float (&qout)[NE]) {
+    using V = typename VecF<NE>::T;
+    const size_t plane = (size_t)c.n * RN;
     const size_t off = (size_t)i * RN + r0;
-    const float4 mq4 = *reinterpret_cast<const float4*>(d.mq + off);
-    float* q = d.q[0];
-    float4 q4 = *reinterpret_cast<const float4*>(q + off);
-    float4 v4[NS];
-    v4[0] = *reinterpret_cast<const float4*>(d.p + off);
+    const V mq4 = *reinterpret_cast<const V*>(c.mq + off);
+    V q4 = *reinterpret_cast<const V*>(c.q + off);
+    V v4[NS];
+    v4[0] = *reinterpret_cast<const V*>(c.p + off);
 #pragma unroll
-    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(d.s + (a - 1) * plane + off);
-    const int flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
-    const uint32_t kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const V*>(c.s + (a - 1) * plane + off);
     float* qa = reinterpret_cast<float*>(&q4);
     const float* mqa = reinterpret_cast<const float*>(&mq4);
-    float samp[4] = {0.f, 0.f, 0.f, 0.f};
+    V sv;
+    float* samp = reinterpret_cast<float*>(&sv);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < NE; ++e) {
         float v[NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[2 * NS];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + d.g.roff, d.g.rk, xi);
-        gle_fused<NS>(qa[e], v, mqa[e], d.g, xi, flags, d.observable, samp[e]);
+        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.g.roff, c.g.rk, xi);
+        samp[e] = 0.f;
+        gle_fused<NS>(qa[e], v, mqa[e], c.g, xi, c.flags, c.observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+        qout[e] = qa[e];
     }
-    *reinterpret_cast<float4*>(q + off) = q4;
-    *reinterpret_cast<float4*>(d.p + off) = v4[0];
+    *reinterpret_cast<V*>(c.q + off) = q4;
+    *reinterpret_cast<V*>(c.p + off) = v4[0];
 #pragma unroll
-    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(d.s + (a - 1) * plane + off) = v4[a];
-    if (d.primed)
-        *reinterpret_cast<float4*>(d.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
-    // force operand for the next step
-    if (kind == 1) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            *reinterpret_cast<float*>(d.bt_hi + swz_offset(r0 + e, i, 32, 4, RN)) = to_tf32_pool(qa[e]);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(qa[e]);
-            const size_t o = swz_offset(r0 + e, i, 64, 2, RN);
-            *reinterpret_cast<__nv_bfloat16*>(d.bt_hi + o) = hb;
-            *reinterpret_cast<__nv_bfloat16*>(d.bt_lo + o) =
-                __float2bfloat16_rn(qa[e] - __bfloat162float(hb));
-        }
-    }
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<V*>(c.s + (a - 1) * plane + off) = v4[a];
+    if (c.primed) *reinterpret_cast<V*>(c.x + off) = sv;
 }
 
-// blockDim (32, 8): item = 32 rows of one problem; the 8 y-threads cover 32 replicas per
-// pass (4 each) and loop over the RN / 32 replica chunks.
-__global__ void __launch_bounds__(256, 2)
+// NE replicas per lane, MINB CTAs of 256 per SM (the register budget).
+template <int NE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
                 int nitems, int RN, int kind) {
-    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
-        const PoolRowItem it = items[j];
-        const PoolDesc& d = desc[it.problem];
-        const int i = it.row0 + threadIdx.x;
-        if (i >= d.n) continue;
-        for (int r0 = threadIdx.y * 4; r0 < RN; r0 += 32) {
-            switch (d.ns) {
-                case 1: pool_gle_rows<1>(d, i, r0, RN, kind); break;
-                case 2: pool_gle_rows<2>(d, i, r0, RN, kind); break;
-                case 3: pool_gle_rows<3>(d, i, r0, RN, kind); break;
-                case 4: pool_gle_rows<4>(d, i, r0, RN, kind); break;
-                default: pool_gle_rows<5>(d, i, r0, RN, kind); break;
+    constexpr int LPR = 32 / NE;          // lanes per row: NE replicas each, 32 per pass
+    __shared__ PoolGleShared cs[8];
+    __shared__ __align__(16) float sq[8][4 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PoolGleShared& c = cs[warp];
+    float* tq = sq[warp];
+    const int gw = blockIdx.x * 8 + warp, nw = gridDim.x * 8;
+    int cur = -1;
+    for (int task = gw; task < nitems * 8; task += nw) {
+        const PoolRowItem it = items[task >> 3];
+        if (it.problem != cur) {
+            const PoolDesc& d = desc[it.problem];
+            __syncwarp();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.g);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&c.g);
+            for (int w = lane; w < (int)(sizeof(GleF32) / 4); w += 32) dst[w] = src[w];
+            if (lane == 0) {
+                c.q = d.q[0];
+                c.p = d.p;
+                c.s = d.s;
+                c.mq = d.mq;
+                c.x = d.x;
+                c.bt_hi = d.bt_hi;
+                c.bt_lo = d.bt_lo;
+                c.n = d.n;
+                c.ns = d.ns;
+                c.primed = d.primed;
+                c.flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
+                c.observable = d.observable;
+                c.kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+            }
+            cur = it.problem;
+            __syncwarp();
+        }
+        const int row = it.row0 + (task & 7) * 4;   // first of the warp's 4 rows
+        for (int rp = 0; rp < RN; rp += 32) {
+#pragma unroll
+            for (int h = 0; h < 4 / NE; ++h) {
+                const int k = h * NE + lane / LPR;     // row within the 4
+                const int i = row + k;
+                const int r0 = rp + (lane % LPR) * NE;
+                float qn[NE];
+#pragma unroll
+                for (int e = 0; e < NE; ++e) qn[e] = 0.f;
+                if (i < c.n) {
+                    switch (c.ns) {
+                        case 1: pool_gle_vec<1, NE>(c, i, r0, RN, qn); break;
+                        case 2: pool_gle_vec<2, NE>(c, i, r0, RN, qn); break;
+                        case 3: pool_gle_vec<3, NE>(c, i, r0, RN, qn); break;
+                        case 4: pool_gle_vec<4, NE>(c, i, r0, RN, qn); break;
+                        default: pool_gle_vec<5, NE>(c, i, r0, RN, qn); break;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < NE; ++e) tq[k * 32 + (lane % LPR) * NE + e] = qn[e];
+            }
+            __syncwarp();
+            const int r = rp + lane;                // this lane's replica
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = tq[m * 32 + lane];
+            __syncwarp();
+            if (kind == 1) {
+                const int chunk = (row & 31) >> 2;
+                const size_t o = (size_t)(row >> 5) * RN * 128 + (size_t)r * 128 +
+                                 (size_t)((chunk ^ (r & 7)) << 4);
+                *reinterpret_cast<float4*>(c.bt_hi + o) =
+                    make_float4(to_tf32_pool(v[0]), to_tf32_pool(v[1]), to_tf32_pool(v[2]),
+                                to_tf32_pool(v[3]));
+            } else {
+                __align__(8) __nv_bfloat16 hv[4], lv[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    hv[m] = __float2bfloat16_rn(v[m]);
+                    lv[m] = __float2bfloat16_rn(v[m] - __bfloat162float(hv[m]));
+                }
+                const int col = (row & 63) * 2;     // byte column in the 128-byte row
+                const size_t o = (size_t)(row >> 6) * RN * 128 + (size_t)r * 128 +
+                                 (size_t)((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+                *reinterpret_cast<uint2*>(c.bt_hi + o) = *reinterpret_cast<const uint2*>(hv);
+                *reinterpret_cast<uint2*>(c.bt_lo + o) = *reinterpret_cast<const uint2*>(lv);
             }
         }
     }
 }
 
-cudaError_t launch_pool_gle(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
-                            int kind, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    const int grid = std::min(nitems, 152 * 12);
-    pool_gle_kernel<<<grid, dim3(32, 8), 0, st>>>(desc, items, nitems, RN, kind);
+template <int NE, int MINB>
+cudaError_t launch_pool_gle_t(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                              int kind, cudaStream_t st) {
+    // persistent: one wave of resident CTAs walks the task list
+    static const int resident = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_gle_kernel<NE, MINB>, 256, 0);
+        return std::max(1, sms * std::max(per, 1));
+    }();
+    const int grid = std::min(nitems, resident);
+    pool_gle_kernel<NE, MINB><<<grid, 256, 0, st>>>(desc, items, nitems, RN, kind);
     return cudaGetLastError();
+}
+
+// Variants (replicas per lane, CTAs per SM): every variant runs the same arithmetic per
+// element, so they give identical results and the pool may time them on real steps.
+cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
+                            int nitems, int RN, int kind, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    if (RN > kPoolMaxRN || (RN & 31)) return cudaErrorInvalidValue;
+    switch (variant) {
+        case 0: return launch_pool_gle_t<4, 2>(desc, items, nitems, RN, kind, st);
+        case 1: return launch_pool_gle_t<2, 3>(desc, items, nitems, RN, kind, st);
+        case 2: return launch_pool_gle_t<2, 4>(desc, items, nitems, RN, kind, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ CSR fused step
@@ -421,60 +518,76 @@ cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int 
 }
 
 // ------------------------------------------------------------------ accumulate, advance, flush
-// One CTA per live problem.  A prologue launch only marks the problem primed.
+// Items of up to kPoolAccChunk tracked pairs, one thread per pair: the thread sums
+// x_i^r x_j^r over the replicas (two contiguous rows of the sample) and adds it to the
+// pair's block partial.  The last item of a problem to finish (a counter in its
+// descriptor, after a fence) advances the problem's counters and, at a block end,
+// folds the block means into the FP64 Welford sums.  A prologue launch only marks the
+// problem primed.
 __global__ void __launch_bounds__(256)
-pool_accum_kernel(PoolDesc* __restrict__ desc, const int* __restrict__ live, int nlive, int RN,
-                  uint32_t* err) {
-    __shared__ int s_take, s_flush;
+pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ items, int nitems,
+                  int RN, uint32_t* err) {
+    __shared__ int s_last, s_flush;
     __shared__ double s_nb;
-    for (int j = blockIdx.x; j < nlive; j += gridDim.x) {
-        PoolDesc& d = desc[live[j]];
-        if (threadIdx.x == 0) {
-            s_take = d.primed && d.nsamp >= d.burnin;
-            s_flush = 0;
-        }
-        __syncthreads();
-        if (d.primed && s_take) {
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            for (int e = warp; e < d.npairs; e += blockDim.x >> 5) {
-                const float* a = d.x + (size_t)d.pairs[2 * e] * RN;
-                const float* b = d.x + (size_t)d.pairs[2 * e + 1] * RN;
-                float acc = 0.f;
-                for (int r = lane; r < RN; r += 32) acc = fmaf(a[r], b[r], acc);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) d.partial[e] += acc;
+    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
+        const PoolAccItem it = items[j];
+        PoolDesc& d = desc[it.problem];
+        const bool take = d.primed && d.nsamp >= d.burnin;
+        const int e = it.e0 + (int)threadIdx.x;
+        if (take && e < it.e1) {
+            const float4* a = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e] * RN);
+            const float4* b = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e + 1] * RN);
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int r = 0; r < RN / 4; r += 2) {
+                const float4 u0 = a[r], v0 = b[r], u1 = a[r + 1], v1 = b[r + 1];
+                acc0 = fmaf(u0.x, v0.x, acc0);
+                acc1 = fmaf(u1.x, v1.x, acc1);
+                acc0 = fmaf(u0.y, v0.y, acc0);
+                acc1 = fmaf(u1.y, v1.y, acc1);
+                acc0 = fmaf(u0.z, v0.z, acc0);
+                acc1 = fmaf(u1.z, v1.z, acc1);
+                acc0 = fmaf(u0.w, v0.w, acc0);
+                acc1 = fmaf(u1.w, v1.w, acc1);
             }
+            d.partial[e] += acc0 + acc1;
         }
+        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
-            if (!d.primed) {
-                d.primed = 1;
-            } else {
-                d.t += 1;
-                d.nsamp += 1;
-                if (s_take) {
-                    d.inblock += 1;
-                    if (d.inblock == d.block) {
-                        s_flush = 1;
-                        s_nb = (double)(d.nblocks + 1);
+            s_last = atomicAdd(&d.done, 1) == it.nchunks - 1;
+            s_flush = 0;
+            if (s_last) {
+                __threadfence();
+                d.done = 0;
+                if (!d.primed) {
+                    d.primed = 1;
+                } else {
+                    d.t += 1;
+                    d.nsamp += 1;
+                    if (take) {
+                        d.inblock += 1;
+                        if (d.inblock == d.block) {
+                            s_flush = 1;
+                            s_nb = (double)(d.nblocks + 1);
+                        }
                     }
                 }
+                if (d.kind == 1) d.cur ^= 1;
             }
-            if (d.kind == 1) d.cur ^= 1;
         }
         __syncthreads();
         if (s_flush) {
+            // partial sums of the other items: read past L1, they were written this launch
             const double inv = 1.0 / ((double)d.block * (double)RN);
             bool bad = false;
-            for (int e = threadIdx.x; e < d.npairs; e += blockDim.x) {
-                const double bm = (double)d.partial[e] * inv;
+            for (int k = threadIdx.x; k < d.npairs; k += blockDim.x) {
+                const double bm = (double)__ldcg(d.partial + k) * inv;
                 bad |= !isfinite(bm);
-                const double dl = bm - d.mean[e];
-                const double mu = d.mean[e] + dl / s_nb;
-                d.m2[e] += dl * (bm - mu);
-                d.mean[e] = mu;
-                d.partial[e] = 0.f;
+                const double dl = bm - d.mean[k];
+                const double mu = d.mean[k] + dl / s_nb;
+                d.m2[k] += dl * (bm - mu);
+                d.mean[k] = mu;
+                d.partial[k] = 0.f;
             }
             if (bad) atomicOr(err, kErrNonFinite);
             __syncthreads();
@@ -487,10 +600,10 @@ pool_accum_kernel(PoolDesc* __restrict__ desc, const int* __restrict__ live, int
     }
 }
 
-cudaError_t launch_pool_accum(PoolDesc* desc, const int* live, int nlive, int RN, uint32_t* err,
-                              cudaStream_t st) {
-    if (nlive <= 0) return cudaSuccess;
-    pool_accum_kernel<<<std::min(nlive, 152 * 8), 256, 0, st>>>(desc, live, nlive, RN, err);
+cudaError_t launch_pool_accum(PoolDesc* desc, const PoolAccItem* items, int nitems, int RN,
+                              uint32_t* err, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    pool_accum_kernel<<<std::min(nitems, 152 * 8), 256, 0, st>>>(desc, items, nitems, RN, err);
     return cudaGetLastError();
 }
 
