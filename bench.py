@@ -281,6 +281,13 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "serving":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "serving stream: the FP64 oracle would need hours of host time to "
+                          "serve the request stream once; per-step oracle baselines are the "
+                          "dense4096, lattice64, small_fp64 and ragged512 reference lines"}),
+              flush=True)
+        return 0
     if args.workload == "ragged512":
         wl = Ragged()
         cb = cpu_baseline_ragged(wl, budget_s=REF_BUDGET_S, steps=args.steps)
@@ -480,6 +487,132 @@ def cpu_baseline_ragged(wl, budget_s=CPU_BUDGET_S, nsample=16, steps=None):
                       f"{done} replica-steps in {t_used:.1f} s"}
 
 
+# ---------------------------------------------------------------------- serving
+class Serving:
+    """Poisson request stream at `rate` per second over an arrival window of `window`
+    seconds.  Each request: 50 % dense SPD (N uniform in [128, 4096], lambda log-uniform
+    in [1, 1e2], Haar Q), 50 % periodic lattice L^3 (L uniform in {16..48}, as the 64^3
+    workload); f = x^-1/2 or Fermi beta = 2 (mu = median lambda = 10 dense, 7 lattice),
+    50 / 50, each with its own fitted GLE; relative accuracy target t_hi or t_lo, 50 / 50;
+    32 tracked elements (16 diagonal, 16 off-diagonal: random pairs dense, nearest
+    neighbours lattice); R = 32 replicas; its own Philox key.  Matrices are drawn from
+    a seeded set of `distinct` dense and lattice matrices generated before the run."""
+
+    name = "serving"
+
+    def __init__(self, rate=200.0, window=1.0, t_hi=0.1, t_lo=0.03, budget=10000, distinct=8):
+        from paper_1402_2095_gb300 import fit
+        self.seed = syn.BASE_SEED + 4
+        g = np.random.default_rng(self.seed)
+        self.rate, self.window, self.t_hi, self.t_lo, self.budget = rate, window, t_hi, t_lo, budget
+        self.arrivals = syn.poisson_arrivals(rate, window, seed=self.seed)
+        self.fits = {k: fit.load_gle(k) for k in ("inv_sqrt_1_100", "fermi_b2_1_100",
+                                                   "inv_sqrt_lattice", "fermi_b2_lattice")}
+        self.dense, self.lattice = [], []
+        for k in range(distinct):
+            n = int(g.integers(128, 4097))
+            M, _, _ = syn.dense_spd(n, 1.0, 100.0, seed=self.seed * 100 + k)
+            self.dense.append(M.astype(np.float32))
+            L = int(g.integers(16, 49))
+            rowptr, col, val = syn.lattice_csr(L, seed=self.seed * 100 + k)
+            self.lattice.append((rowptr, col, val.astype(np.float32), L ** 3, L))
+        self.reqs = []
+        for j in range(len(self.arrivals)):
+            dense = bool(g.integers(0, 2))
+            k = int(g.integers(0, distinct))
+            fermi = bool(g.integers(0, 2))
+            target = self.t_hi if g.integers(0, 2) else self.t_lo
+            if dense:
+                n = self.dense[k].shape[0]
+                fname = "fermi_b2_1_100" if fermi else "inv_sqrt_1_100"
+                pairs = np.concatenate([syn.diag_pairs(n)[g.choice(n, 16, replace=False)],
+                                        syn.random_pairs(n, 16, seed=self.seed + j)])
+                mat = {"M": self.dense[k]}
+            else:
+                rowptr, col, val, n, L = self.lattice[k]
+                fname = "fermi_b2_lattice" if fermi else "inv_sqrt_lattice"
+                nn = syn.lattice_nn_pairs(L)
+                pairs = np.concatenate([syn.diag_pairs(n)[g.choice(n, 16, replace=False)],
+                                        nn[g.choice(len(nn), 16, replace=False)]])
+                mat = {"csr": (rowptr, col, val, n)}
+            a_p, c_p, dt, _ = self.fits[fname]
+            self.reqs.append(dict(mat, a_p=a_p, c_p=c_p, dt=dt, seed=self.seed * 10000 + j,
+                                  block=1000, pairs=pairs, target=target, max_steps=budget))
+        self.label = (f"Poisson {rate:g} req/s over {window:g} s ({len(self.reqs)} requests); 50% "
+                      f"dense N~U[128,4096] / 50% lattice L~U{{16..48}}; f in {{x^-1/2, Fermi b=2}}; "
+                      f"targets {t_hi:g}/{t_lo:g} (normwise rel. error bar), budget {budget} "
+                      f"steps; 32 elements; R=32 each")
+
+
+def run_serving(args, rank, world, local):
+    import torch
+    from paper_1402_2095_gb300 import Server
+    wl = Serving(rate=args.rate, window=args.window, budget=args.budget)
+    srv = Server(args.serve_gb << 30, replicas=32, precision="bf16x3", max_problems=1024,
+                 graph_steps=0, chunk_steps=1000, min_blocks=4, max_bypass=8)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ids, nxt = [], 0
+    c0 = srv.clock()
+    steps_total, launches, peak_used, busy = 0, 0, 0, 0.0
+    t_end_limit = c0 + args.serve_timeout
+    while True:
+        now = srv.clock() - c0
+        while nxt < len(wl.reqs) and wl.arrivals[nxt] <= now:
+            ids.append(srv.submit(**wl.reqs[nxt]))
+            nxt += 1
+        c = srv.step()
+        if c["running"] or c["admitted"]:
+            steps_total += 1000
+            launches += 3 * 1000
+        peak_used = max(peak_used, c["used_bytes"])
+        if nxt == len(wl.reqs) and c["running"] == 0 and c["queued"] == 0:
+            break
+        if srv.clock() > t_end_limit:
+            break
+        if c["running"] == 0 and c["queued"] == 0 and nxt < len(wl.reqs):
+            # idle until the next arrival
+            time.sleep(max(0.0, min(0.01, wl.arrivals[nxt] - (srv.clock() - c0))))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    wall = srv.clock() - c0
+    lat, states, rsteps, relerr = [], {}, [], []
+    for j, rid in enumerate(ids):
+        info, v, e = srv.result(rid)
+        states[info["state"]] = states.get(info["state"], 0) + 1
+        if info["state"] in ("done", "budget"):
+            lat.append(info["t_done"] - c0 - wl.arrivals[j])
+            rsteps.append(info["steps"])
+            relerr.append(info["rel_err"])
+    lat = np.asarray(lat)
+    replica_steps = 32 * float(np.sum(rsteps))
+    srv.close()
+    p50 = float(np.percentile(lat, 50)) if lat.size else None
+    p99 = float(np.percentile(lat, 99)) if lat.size else None
+    line = {
+        "metric": "p99 request latency", "value": p99, "unit": "s", "n_gpus": world,
+        "steps": steps_total, "warmup": 0, "ms_per_step": wall / max(steps_total, 1) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.label, "requests": len(wl.reqs), "submitted": len(ids),
+                   "states": states, "chunk_steps": 1000, "min_blocks": 4,
+                   "workspace_gb": args.serve_gb, "peak_used_gb": peak_used / 2 ** 30,
+                   "l2": "resident working set of all admitted requests >> L2"},
+        "latency_s": {"p50": p50, "p99": p99, "mean": float(lat.mean()) if lat.size else None,
+                      "max": float(lat.max()) if lat.size else None},
+        "throughput": {"requests_per_s": len(lat) / wall, "replica_steps_per_s": replica_steps / wall,
+                       "wall_s": wall},
+        "retired_rel_err": {"median": float(np.median(relerr)) if relerr else None},
+        "gpu_launches": launches, "clocks": clk,
+        "e2e": {"value": p99, "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "latency is end to end: host matrices submitted through the public "
+                        "API, results read back on retirement"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -488,7 +621,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense4096",
-                    choices=["dense4096", "small_fp64", "lattice64", "ragged512"])
+                    choices=["dense4096", "small_fp64", "lattice64", "ragged512", "serving"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--window", type=float, default=1.0, help="serving: arrival window (s)")
+    ap.add_argument("--budget", type=int, default=10000, help="serving: step budget per request")
+    ap.add_argument("--serve-gb", type=int, default=64, help="serving: pool workspace (GiB)")
+    ap.add_argument("--serve-timeout", type=float, default=300.0, help="serving: wall limit (s)")
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -509,8 +647,8 @@ def main():
 
     from paper_1402_2095_gb300 import FTH, build
     build.build()
-    if args.workload == "ragged512":
-        rc = run_ragged(args, rank, world, local)
+    if args.workload in ("ragged512", "serving"):
+        rc = (run_ragged if args.workload == "ragged512" else run_serving)(args, rank, world, local)
         if world > 1:
             dist.destroy_process_group()
         return rc

@@ -292,6 +292,13 @@ fth_status fth_pool_elements(fth_pool* pool, int64_t handle, const int64_t* pair
  * [R][n], s [R][s][n].  Synchronises the stream. */
 fth_status fth_pool_get_state(fth_pool* pool, int64_t handle, int plane, double* host);
 
+/* Convergence of every problem in one device pass: for each handle slot h
+ * (0 <= h < max_problems), rel_err[h] = sqrt(sum_e sigma_e^2) / sqrt(sum_e mean_e^2)
+ * over the problem's tracked elements (sigma_e the block error bar, mean_e the mean of
+ * the complete blocks; NaN before 2 blocks, and for empty slots) and blocks[h] = its
+ * number of complete blocks (-1 for empty slots; may be NULL).  Synchronises. */
+fth_status fth_pool_progress(fth_pool* pool, double* rel_err, int64_t* blocks);
+
 /* Counters of one problem (steps, samples, blocks ...).  Synchronises the stream. */
 fth_status fth_pool_problem_info(fth_pool* pool, int64_t handle, fth_info_t* info);
 
@@ -308,6 +315,65 @@ enum fth_pool_kernel { FTH_PK_FORCE = 0, FTH_PK_GLE = 1, FTH_PK_CSR = 2, FTH_PK_
 fth_status fth_pool_profile(fth_pool* pool, int64_t steps, double* ms, int64_t* launches);
 const char* fth_pool_last_error(const fth_pool* pool);
 void fth_pool_destroy(fth_pool* pool);
+
+/* ----------------------------------------------------------------------------------
+ * Serving loop over a pool: requests are queued on submit, admitted into the pool when
+ * a slot and enough workspace are free (arrival order; a request that does not fit is
+ * passed by later ones at most max_bypass times), stepped together with all others
+ * (continuous batching), and retired when the normwise relative error bar of their
+ * tracked elements (fth_pool_progress) is <= their target with at least min_blocks
+ * complete blocks, or when their step budget is spent.  Host code only; the GPU work
+ * is the pool's.  Results are those the same problem gives alone in a pool.
+ * ---------------------------------------------------------------------------------- */
+typedef struct fth_server fth_server;
+
+enum fth_request_state { FTH_REQ_QUEUED = 0, FTH_REQ_RUNNING = 1, FTH_REQ_DONE = 2,
+                         FTH_REQ_BUDGET = 3 /* retired at max_steps above target */,
+                         FTH_REQ_FAILED = 4 /* rejected by validation */ };
+
+typedef struct {
+    fth_pool_options pool;
+    int64_t chunk_steps;    /* steps between admission / retirement checks (>= 1)          */
+    int64_t min_blocks;     /* complete blocks needed before a target counts (>= 2)        */
+    int64_t max_bypass;     /* times a waiting request may be passed by later ones         */
+} fth_server_options;
+
+typedef struct {
+    int64_t admitted, retired, running, queued;  /* this step; now                      */
+    int64_t steps;                               /* server steps so far                 */
+    size_t used_bytes, slab_bytes;               /* pool workspace occupancy            */
+} fth_server_counts;
+
+typedef struct {
+    int state;              /* enum fth_request_state                                      */
+    int64_t steps;          /* steps run (so far)                                          */
+    double rel_err;         /* normwise relative error bar at the last check               */
+    double t_submit, t_admit, t_done;   /* seconds on the server clock                      */
+    int64_t npairs;
+} fth_request_info;
+
+/* Create a server and its pool on `workspace` (as fth_pool_create). */
+fth_status fth_server_create(const fth_server_options* opt, void* workspace, size_t bytes,
+                             fth_server** out);
+
+/* Queue a request (copies M and the pairs; po->npairs >= 1).  target > 0: relative
+ * accuracy wanted; max_steps: step budget (0 = none).  *id numbers requests from 0. */
+fth_status fth_server_submit(fth_server* srv, const fth_matrix* M, const fth_gle* gle,
+                             const fth_problem_options* po, double target, int64_t max_steps,
+                             int64_t* id);
+
+/* One serving iteration: admit, run chunk_steps steps, retire.  Synchronises. */
+fth_status fth_server_step(fth_server* srv, fth_server_counts* counts);
+
+/* State of a request; when retired, its tracked elements (in its pair order) and their
+ * error bars are copied to values / errbars (npairs each, may be NULL). */
+fth_status fth_server_result(fth_server* srv, int64_t id, fth_request_info* info,
+                             double* values, double* errbars);
+
+double fth_server_clock(const fth_server* srv);     /* seconds since creation           */
+fth_pool* fth_server_pool(fth_server* srv);         /* the server's pool (stats)        */
+const char* fth_server_last_error(const fth_server* srv);
+void fth_server_destroy(fth_server* srv);
 
 /* Library version string. */
 const char* fth_version(void);

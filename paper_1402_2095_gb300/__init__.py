@@ -2,4 +2,4 @@
 GLE dynamics (Nava, Ceriotti, Dryzun, Parrinello).  The compute path is libfth.so
 (hand-written sm_103a CUDA behind the C ABI of include/fth.h); this package holds
 its build script, the ctypes binding and the host-side GLE fitter."""
-from .binding import FTH, FthError, Pool, gle_propagator, load  # noqa: F401
+from .binding import FTH, FthError, Pool, Server, gle_propagator, load  # noqa: F401

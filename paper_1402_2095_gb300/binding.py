@@ -32,7 +32,10 @@ EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_g
            "fth_dense_step_noalloc", "fth_pool_create", "fth_pool_footprint", "fth_pool_add",
            "fth_pool_remove", "fth_pool_run", "fth_pool_elements", "fth_pool_get_state",
            "fth_pool_problem_info",
-           "fth_pool_stats", "fth_pool_profile", "fth_pool_last_error", "fth_pool_destroy")
+           "fth_pool_stats", "fth_pool_profile", "fth_pool_progress", "fth_pool_last_error",
+           "fth_pool_destroy", "fth_server_create", "fth_server_submit", "fth_server_step",
+           "fth_server_result", "fth_server_clock", "fth_server_pool", "fth_server_last_error",
+           "fth_server_destroy")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense")
 
@@ -80,6 +83,26 @@ class fth_pool_stats_t(ctypes.Structure):
                 ("tuned_variant", ctypes.c_int), ("tuned_grid", ctypes.c_int),
                 ("tuned_us", ctypes.c_double), ("gle_variant", ctypes.c_int),
                 ("gle_us", ctypes.c_double), ("graphs", ctypes.c_int64)]
+
+
+class fth_server_options(ctypes.Structure):
+    _fields_ = [("pool", fth_pool_options), ("chunk_steps", ctypes.c_int64),
+                ("min_blocks", ctypes.c_int64), ("max_bypass", ctypes.c_int64)]
+
+
+class fth_server_counts(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("retired", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("queued", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("used_bytes", ctypes.c_size_t), ("slab_bytes", ctypes.c_size_t)]
+
+
+class fth_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("steps", ctypes.c_int64), ("rel_err", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("npairs", ctypes.c_int64)]
+
+
+REQUEST_STATE = {0: "queued", 1: "running", 2: "done", 3: "budget", 4: "failed"}
 
 
 class fth_info_t(ctypes.Structure):
@@ -130,6 +153,15 @@ def load(path: str = LIB_PATH):
         "fth_pool_problem_info": ([P, I64, P], INT),
         "fth_pool_stats": ([P, P], INT),
         "fth_pool_profile": ([P, I64, P, P], INT),
+        "fth_pool_progress": ([P, P, P], INT),
+        "fth_server_create": ([P, P, ctypes.c_size_t, P], INT),
+        "fth_server_submit": ([P, P, P, P, D, I64, P], INT),
+        "fth_server_step": ([P, P], INT),
+        "fth_server_result": ([P, I64, P, P, P], INT),
+        "fth_server_clock": ([P], D),
+        "fth_server_pool": ([P], P),
+        "fth_server_last_error": ([P], ctypes.c_char_p),
+        "fth_server_destroy": ([P], None),
         "fth_pool_last_error": ([P], ctypes.c_char_p),
         "fth_pool_destroy": ([P], None),
     }
@@ -385,6 +417,7 @@ class Pool:
         o.graph_steps = int(graph_steps)
         o.stream = self.stream.cuda_stream
         self.replicas = int(replicas)
+        self.max_problems = int(max_problems)
         h = ctypes.c_void_p()
         _check(L.fth_pool_create(ctypes.byref(o), self.workspace.data_ptr(), self.workspace.numel(),
                                  ctypes.byref(h)))
@@ -478,10 +511,108 @@ class Pool:
                     self.pool)
         return {k: (float(ms[c]), int(cnt[c])) for c, k in enumerate(self.POOL_KERNELS) if cnt[c]}
 
+    def progress(self):
+        """(rel_err, blocks) per handle slot: normwise relative error bar over each
+        problem's tracked elements (NaN before 2 blocks / empty slot), complete blocks."""
+        n = self.max_problems
+        rel = np.zeros(n)
+        blk = np.zeros(n, dtype=np.int64)
+        _pool_check(load().fth_pool_progress(self.pool, rel.ctypes.data, blk.ctypes.data), self.pool)
+        return rel, blk
+
     def close(self):
         if getattr(self, "pool", None):
             load().fth_pool_destroy(self.pool)
             self.pool = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------- serving loop
+class Server:
+    """Continuous-batching serving loop over a pool (C++ in libfth): submit requests at
+    any time, call step() repeatedly; each step admits what fits, runs chunk_steps steps
+    of everything admitted and retires what met its target."""
+
+    def __init__(self, workspace_bytes, *, replicas=32, precision="bf16x3", max_problems=256,
+                 graph_steps=0, chunk_steps=500, min_blocks=4, max_bypass=8, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(int(workspace_bytes), dtype=torch.uint8, device="cuda")
+        o = fth_server_options()
+        o.pool.replicas = int(replicas)
+        o.pool.precision = PRECISION[precision]
+        o.pool.max_problems = int(max_problems)
+        o.pool.graph_steps = int(graph_steps)
+        o.pool.stream = self.stream.cuda_stream
+        o.chunk_steps = int(chunk_steps)
+        o.min_blocks = int(min_blocks)
+        o.max_bypass = int(max_bypass)
+        h = ctypes.c_void_p()
+        _check(load().fth_server_create(ctypes.byref(o), self.workspace.data_ptr(),
+                                        self.workspace.numel(), ctypes.byref(h)))
+        self.srv = h
+        self.replicas = int(replicas)
+        self._np = {}
+
+    def _err(self, st):
+        if st != FTH_OK:
+            msg = load().fth_server_last_error(self.srv)
+            raise FthError(st, msg.decode() if msg else "")
+
+    def submit(self, M=None, csr=None, *, a_p, c_p, dt, target, max_steps=0, seed=0, burnin=0,
+               block=1000, observable="p", pairs, replica_offset=0):
+        keep = []
+        mat = _matrix_struct(M, csr, keep)
+        gle = make_gle(a_p, c_p)
+        po = fth_problem_options()
+        po.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        po.dt = float(dt)
+        po.burnin = int(burnin)
+        po.block = int(block)
+        po.observable = OBSERVABLE[observable]
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        po.pairs = pr.ctypes.data
+        po.npairs = pr.shape[0]
+        po.replica_offset = int(replica_offset)
+        rid = ctypes.c_int64(-1)
+        self._err(load().fth_server_submit(self.srv, ctypes.byref(mat), ctypes.byref(gle),
+                                           ctypes.byref(po), float(target), int(max_steps),
+                                           ctypes.byref(rid)))
+        self._np[int(rid.value)] = pr.shape[0]
+        return int(rid.value)
+
+    def step(self) -> dict:
+        c = fth_server_counts()
+        self._err(load().fth_server_step(self.srv, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in fth_server_counts._fields_}
+
+    def result(self, rid):
+        """(info dict, values, errbars); values/errbars are None until retired."""
+        info = fth_request_info()
+        k = self._np[int(rid)]
+        vals = np.full(k, np.nan)
+        errs = np.full(k, np.nan)
+        self._err(load().fth_server_result(self.srv, int(rid), ctypes.byref(info),
+                                           vals.ctypes.data, errs.ctypes.data))
+        d = {f: getattr(info, f) for f, _ in fth_request_info._fields_}
+        d["state"] = REQUEST_STATE[d["state"]]
+        if d["state"] in ("done", "budget"):
+            return d, vals, errs
+        return d, None, None
+
+    def clock(self) -> float:
+        return load().fth_server_clock(self.srv)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            load().fth_server_destroy(self.srv)
+            self.srv = None
 
     def __del__(self):
         try:

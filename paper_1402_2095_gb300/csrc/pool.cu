@@ -23,39 +23,6 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 int64_t rup(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
 
-uint16_t bf16_rne_p(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-float bf16_f_p(uint16_t h) {
-    const uint32_t u = (uint32_t)h << 16;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-float tf32_rna_p(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    if ((u & 0x7F800000u) != 0x7F800000u) {
-        u += 0x1000u;
-        u &= ~0x1FFFu;
-    }
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
-}
-
-// Byte offset of element (i, k) of M (np x np) in the pre-swizzled blocked layout
-// [np/128][np/ks][128 rows][128 bytes], 16-byte chunk c of row r at chunk c ^ (r & 7).
-size_t swz_block_offset(int64_t i, int64_t k, int64_t np, int64_t ks, int64_t esz) {
-    const int64_t rb = i / 128, r = i % 128, kb = k / ks;
-    const int64_t col = (k % ks) * esz;
-    return (size_t)(((rb * (np / ks) + kb) * 128 + r) * 128 + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15)));
-}
-
 struct Layout {
     size_t a_hi = 0, a_lo = 0, bt_hi = 0, bt_lo = 0, mq = 0, q0 = 0, q1 = 0, p = 0, s = 0, x = 0;
     size_t rowptr = 0, col = 0, val = 0, pairs = 0, partial = 0, mean = 0, m2 = 0, total = 0;
@@ -125,6 +92,9 @@ struct fth_pool {
     PoolForceItem* d_force = nullptr;
     PoolRowItem* d_rows = nullptr;     // dense rows, then CSR rows
     PoolAccItem* d_acc = nullptr;
+    int* d_live = nullptr;                // live slots (progress kernel)
+    double* d_prog = nullptr;             // [max_problems][2] progress output
+    uint8_t* stage = nullptr;             // kPoolStageBytes for dense uploads
     uint32_t* d_err = nullptr;
     int64_t cap_force = 0, cap_rows = 0, cap_acc = 0;
     size_t slab_begin = 0, slab_end = 0;
@@ -255,6 +225,9 @@ fth_status rebuild_lists(fth_pool* P) {
     if (!P->h_rows.empty())
         PCK(cudaMemcpyAsync(P->d_rows, P->h_rows.data(), P->h_rows.size() * sizeof(PoolRowItem),
                             cudaMemcpyHostToDevice, P->stream), "h2d row items");
+    if (!P->h_live.empty())
+        PCK(cudaMemcpyAsync(P->d_live, P->h_live.data(), P->h_live.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, P->stream), "h2d live slots");
     if (!P->h_acc.empty())
         PCK(cudaMemcpyAsync(P->d_acc, P->h_acc.data(), P->h_acc.size() * sizeof(PoolAccItem),
                             cudaMemcpyHostToDevice, P->stream), "h2d accumulate items");
@@ -414,6 +387,12 @@ fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t 
     o = a256(o + sizeof(PoolRowItem) * (size_t)P->cap_rows);
     const size_t off_acc = o;
     o = a256(o + sizeof(PoolAccItem) * (size_t)P->cap_acc);
+    const size_t off_live = o;
+    o = a256(o + sizeof(int) * (size_t)P->max_problems);
+    const size_t off_prog = o;
+    o = a256(o + 2 * sizeof(double) * (size_t)P->max_problems);
+    const size_t off_stage = o;
+    o = a256(o + kPoolStageBytes);
     const size_t off_err = o;
     o = a256(o + 256);
     if (o >= bytes) {
@@ -425,6 +404,9 @@ fth_status fth_pool_create(const fth_pool_options* opt, void* workspace, size_t 
     P->d_rows = reinterpret_cast<PoolRowItem*>(P->ws + off_rows);
     P->d_acc = reinterpret_cast<PoolAccItem*>(P->ws + off_acc);
     P->d_err = reinterpret_cast<uint32_t*>(P->ws + off_err);
+    P->stage = P->ws + off_stage;
+    P->d_live = reinterpret_cast<int*>(P->ws + off_live);
+    P->d_prog = reinterpret_cast<double*>(P->ws + off_prog);
     P->slab_begin = o;
     P->slab_end = bytes & ~size_t(255);
     P->free_list[P->slab_begin] = P->slab_end - P->slab_begin;
@@ -521,51 +503,47 @@ fth_status fth_pool_add(fth_pool* P, const fth_matrix* M, const fth_gle* gle,
         cudaStreamSynchronize(P->stream) != cudaSuccess)
         return fail_free(FTH_E_CUDA, "zero problem memory");
 
-    // host copy of M in FP64 (validation, conversion)
+    // dense M: checked on the host (diagonal), converted on the device row block by row
+    // block (FP32 / FP64 rows staged through the pool's staging buffer when on the host)
     const size_t esz_in = M->dtype == FTH_F64 ? 8 : 4;
     auto value_at = [&](const std::vector<uint8_t>& raw, size_t k) {
         return esz_in == 8 ? reinterpret_cast<const double*>(raw.data())[k]
                            : (double)reinterpret_cast<const float*>(raw.data())[k];
     };
     if (M->kind == FTH_DENSE) {
-        std::vector<uint8_t> raw((size_t)n * n * esz_in);
+        std::vector<uint8_t> diag((size_t)n * esz_in);
         if (M->on_device) {
-            if (cudaMemcpy(raw.data(), M->values, raw.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-                return fail_free(FTH_E_CUDA, "d2h M");
+            if (cudaMemcpy2D(diag.data(), esz_in, M->values, (size_t)(n + 1) * esz_in, esz_in, (size_t)n,
+                             cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail_free(FTH_E_CUDA, "d2h diagonal");
         } else {
-            std::memcpy(raw.data(), M->values, raw.size());
+            for (int64_t i = 0; i < n; ++i)
+                std::memcpy(diag.data() + i * esz_in,
+                            static_cast<const uint8_t*>(M->values) + (size_t)(i * n + i) * esz_in, esz_in);
         }
         for (int64_t i = 0; i < n; ++i)
-            if (!(value_at(raw, (size_t)i * n + i) > 0.0))
+            if (!(value_at(diag, (size_t)i) > 0.0))
                 return fail_free(FTH_E_NOT_SPD, "M has a non-positive diagonal entry");
-        const int64_t np = d.np;
         d.a_hi = base + L.a_hi;
         d.bt_hi = base + L.bt_hi;
         if (P->prec == FTH_PREC_BF16X3) {
             d.a_lo = base + L.a_lo;
             d.bt_lo = base + L.bt_lo;
-            std::vector<uint8_t> hi((size_t)np * np * 2, 0), lo((size_t)np * np * 2, 0);
-            for (int64_t i = 0; i < n; ++i)
-                for (int64_t k = 0; k < n; ++k) {
-                    const float x = (float)value_at(raw, (size_t)i * n + k);
-                    const uint16_t h = bf16_rne_p(x);
-                    const uint16_t l = bf16_rne_p(x - bf16_f_p(h));
-                    const size_t o = swz_block_offset(i, k, np, 64, 2);
-                    std::memcpy(hi.data() + o, &h, 2);
-                    std::memcpy(lo.data() + o, &l, 2);
-                }
-            if (cudaMemcpy(d.a_hi, hi.data(), hi.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(d.a_lo, lo.data(), lo.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                return fail_free(FTH_E_CUDA, "h2d M");
-        } else {
-            std::vector<uint8_t> hi((size_t)np * np * 4, 0);
-            for (int64_t i = 0; i < n; ++i)
-                for (int64_t k = 0; k < n; ++k) {
-                    const float x = tf32_rna_p((float)value_at(raw, (size_t)i * n + k));
-                    std::memcpy(hi.data() + swz_block_offset(i, k, np, 32, 4), &x, 4);
-                }
-            if (cudaMemcpy(d.a_hi, hi.data(), hi.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                return fail_free(FTH_E_CUDA, "h2d M");
+        }
+        const int rows_per = (int)std::max<int64_t>(1, (int64_t)(kPoolStageBytes / ((size_t)n * esz_in)));
+        for (int64_t r0 = 0; r0 < n; r0 += rows_per) {
+            const int nr = (int)std::min<int64_t>(rows_per, n - r0);
+            const uint8_t* src = static_cast<const uint8_t*>(M->values) + (size_t)r0 * n * esz_in;
+            const void* dsrc = src;
+            if (!M->on_device) {
+                if (cudaMemcpyAsync(P->stage, src, (size_t)nr * n * esz_in, cudaMemcpyHostToDevice,
+                                    P->stream) != cudaSuccess)
+                    return fail_free(FTH_E_CUDA, "h2d M rows");
+                dsrc = P->stage;
+            }
+            if (launch_pool_convert(dsrc, esz_in == 8, (int)n, d.np, (int)r0, nr, P->kind_tc,
+                                    d.a_hi, d.a_lo, P->stream) != cudaSuccess)
+                return fail_free(FTH_E_CUDA, "convert M");
         }
     } else {
         const int64_t nnz = M->nnz;
@@ -711,6 +689,31 @@ fth_status fth_pool_profile(fth_pool* P, int64_t steps, double* ms, int64_t* lau
     }
     for (auto& e : ev) cudaEventDestroy(e);
     return st;
+}
+
+fth_status fth_pool_progress(fth_pool* P, double* rel_err, int64_t* blocks) {
+    if (!P || !rel_err) return FTH_E_INVALID_ARG;
+    if (P->dirty) {
+        const fth_status st = rebuild_lists(P);
+        if (st != FTH_OK) return st;
+    }
+    const int64_t nslot = P->max_problems;
+    for (int64_t h = 0; h < nslot; ++h) {
+        rel_err[h] = NAN;
+        if (blocks) blocks[h] = -1;
+    }
+    if (P->h_live.empty()) return FTH_OK;
+    std::vector<double> buf((size_t)nslot * 2);
+    PCK(launch_pool_progress(P->d_desc, P->d_live, (int)P->h_live.size(), P->d_prog, P->stream),
+        "progress");
+    PCK(cudaMemcpyAsync(buf.data(), P->d_prog, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        P->stream), "d2h progress");
+    PCK(cudaStreamSynchronize(P->stream), "sync");
+    for (int h : P->h_live) {
+        rel_err[h] = buf[2 * (size_t)h];
+        if (blocks) blocks[h] = (int64_t)buf[2 * (size_t)h + 1];
+    }
+    return FTH_OK;
 }
 
 fth_status fth_pool_get_state(fth_pool* P, int64_t h, int plane, double* host) {

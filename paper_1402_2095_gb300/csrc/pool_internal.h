@@ -67,6 +67,11 @@ cudaError_t launch_pool_force(int kind, int rn, int variant, const PoolDesc* des
                               const PoolForceItem* items, int nitems, int grid, uint32_t* err,
                               cudaStream_t st);
 int pool_force_max_ctas_per_sm(int kind, int rn, int variant);
+cudaError_t launch_pool_convert(const void* src, int f64, int n, int np, int r0, int nr, int kind,
+                                uint8_t* a_hi, uint8_t* a_lo, cudaStream_t st);
+cudaError_t launch_pool_progress(const PoolDesc* desc, const int* live, int nlive, double* out,
+                                 cudaStream_t st);
+constexpr size_t kPoolStageBytes = size_t(16) << 20;   // host-to-device staging of M rows
 constexpr int kPoolGleVariants = 3;
 cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
                             int nitems, int RN, int kind, cudaStream_t st);

@@ -517,6 +517,93 @@ cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ convergence
+// One CTA per live problem: over its tracked pairs, the normwise relative error bar of
+// the block average, sqrt(sum_e M2_e / (nb (nb - 1))) / sqrt(sum_e mean_e^2), and the
+// number nb of complete blocks, written to out[2 slot], out[2 slot + 1].
+__global__ void __launch_bounds__(256)
+pool_progress_kernel(const PoolDesc* __restrict__ desc, const int* __restrict__ live, int nlive,
+                     double* __restrict__ out) {
+    __shared__ double red[2][8];
+    for (int j = blockIdx.x; j < nlive; j += gridDim.x) {
+        const int slot = live[j];
+        const PoolDesc& d = desc[slot];
+        const double nb = (double)d.nblocks;
+        double s2 = 0.0, mm = 0.0;
+        if (nb >= 2.0)
+            for (int e = threadIdx.x; e < d.npairs; e += blockDim.x) {
+                s2 += d.m2[e];
+                mm += d.mean[e] * d.mean[e];
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            mm += __shfl_xor_sync(0xffffffffu, mm, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = s2;
+            red[1][threadIdx.x >> 5] = mm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                a += red[0][w];
+                b += red[1][w];
+            }
+            out[2 * slot] = nb >= 2.0 && b > 0.0 ? sqrt(a / (nb * (nb - 1.0))) / sqrt(b) : NAN;
+            out[2 * slot + 1] = nb;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pool_progress(const PoolDesc* desc, const int* live, int nlive, double* out,
+                                 cudaStream_t st) {
+    if (nlive <= 0) return cudaSuccess;
+    pool_progress_kernel<<<std::min(nlive, 152 * 4), 256, 0, st>>>(desc, live, nlive, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ operand conversion
+// Rows [r0, r0 + nr) of a dense matrix (row-major, n columns, FP32 or FP64 at `src`,
+// whose row 0 is row r0) into the force operand layout: element (i, k) at byte
+// ((i / 128 * (np / KS) + k / KS) * 128 + i % 128) * 128 + swizzled column, where the
+// 16-byte chunk c of row r sits at chunk position c ^ (r & 7).  BF16X3 (kind 2) stores
+// hi = bf16(x) and lo = bf16(x - hi), both round-to-nearest-even; TF32 (kind 1) stores
+// x rounded to nearest (ties away), as the tensor core reads it.
+__global__ void pool_convert_kernel(const void* __restrict__ src, int f64, int n, int np,
+                                    int r0, int nr, int kind, uint8_t* __restrict__ a_hi,
+                                    uint8_t* __restrict__ a_lo) {
+    const int64_t total = (int64_t)nr * n;
+    const int ks = kind == 1 ? 32 : 64, esz = kind == 1 ? 4 : 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = r0 + e / n, k = e % n;
+        const float x = f64 ? (float)static_cast<const double*>(src)[e]
+                            : static_cast<const float*>(src)[e];
+        const int64_t r = i & 127, col = (k % ks) * esz;
+        const size_t o = (size_t)((((i >> 7) * (np / ks) + k / ks) * 128 + r) * 128 +
+                                  ((((col >> 4) ^ (r & 7)) << 4) | (col & 15)));
+        if (kind == 1) {
+            *reinterpret_cast<float*>(a_hi + o) = to_tf32_pool(x);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *reinterpret_cast<__nv_bfloat16*>(a_hi + o) = h;
+            *reinterpret_cast<__nv_bfloat16*>(a_lo + o) = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
+    }
+}
+
+cudaError_t launch_pool_convert(const void* src, int f64, int n, int np, int r0, int nr, int kind,
+                                uint8_t* a_hi, uint8_t* a_lo, cudaStream_t st) {
+    if (nr <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)nr * n;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    pool_convert_kernel<<<grid, 256, 0, st>>>(src, f64, n, np, r0, nr, kind, a_hi, a_lo);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ accumulate, advance, flush
 // Items of up to kPoolAccChunk tracked pairs, one thread per pair: the thread sums
 // x_i^r x_j^r over the replicas (two contiguous rows of the sample) and adds it to the

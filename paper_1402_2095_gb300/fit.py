@@ -210,6 +210,9 @@ FITS = {
     "fermi_b5_1_1000": ("fermi", (5.0, 10 ** 1.5), 1.0, 1000.0, 3, 400),
     "inv_sqrt_1_100": ("inv_sqrt", (), 1.0, 100.0, 6, 1500),
     "fermi_b2_lattice": ("fermi", (2.0, 7.0), 0.5, 14.5, 3, 400),
+    # request mix of the serving loop: the two functions on both spectral ranges
+    "fermi_b2_1_100": ("fermi", (2.0, 10.0), 1.0, 100.0, 3, 400),
+    "inv_sqrt_lattice": ("inv_sqrt", (), 0.5, 14.5, 4, 800),
 }
 
 

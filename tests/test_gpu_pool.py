@@ -150,7 +150,7 @@ def test_pool_statistics_match_oracle():
 def test_pool_admission_and_reuse():
     M = _dense(256, seed=50)
     a, c = _gle(4, 51)
-    pool = _pool(replicas=32, workspace=12 << 20)
+    pool = _pool(replicas=32, workspace=32 << 20)
     need = pool.footprint(M, a_p=a, c_p=c, dt=0.01)
     slab = pool.stats()["slab_bytes"]
     from paper_1402_2095_gb300 import FthError

@@ -24,7 +24,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(ROOT, "include", "fth.h")).read()
-    declared = set(re.findall(r"^\s*(?:fth_status|const char\s*\*|void)\s+(fth_\w+)\s*\(", hdr,
+    declared = set(re.findall(r"^\s*(?:fth_status|const char\s*\*|void|double|fth_pool\s*\*)\s+(fth_\w+)\s*\(", hdr,
                               flags=re.M))
     assert declared == set(B.EXPORTS)
     for name in declared:
