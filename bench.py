@@ -277,6 +277,64 @@ def cpu_baseline(wl, budget_s=CPU_BUDGET_S):
                       f"{steps} steps in {el:.1f} s"}
 
 
+def exact_target(wl, pairs, vals, errs, steps, ms_per_step):
+    """Part of the CPU baseline: the oracle's exact route (FP64 eigendecomposition, per-mode
+    discrete response of the fitted GLE), timed, and the GPU estimate's error against it.
+
+    rel_err: ||est - E[est]|| / ||g|| over the tracked elements, E[est] the exact expected
+    running mean after `steps` samples from the zero state; sigma_rel: the same norm of
+    the block error bars; time_to_1e-3: steps x (sigma_rel / 1e-3)^2 x the GPU step time
+    (the statistical error falls as steps^-1/2); transient: ||E[est] - g|| / ||g||;
+    fit_bias: ||g - f|| / ||f|| (the fitted GLE against the wanted function)."""
+    if wl.csr is not None:
+        return {"skipped": "the exact lattice target needs a Chebyshev expansion per tracked "
+                           "element (1,048,576 of them): beyond the baseline's time budget"}
+    from oracle import gle, matfun
+    M = wl.oracle_matrix()["M"]
+    t0 = time.perf_counter()
+    lam, U = np.linalg.eigh(M)
+    t_eigh = time.perf_counter() - t0
+    T, S = gle.propagator(wl.a_p, wl.c_p, wl.dt)
+    g = gle.mode_response(lam, T, S, wl.dt)
+    gm = gle.mode_response_mean(lam, T, S, wl.dt, 0, steps)
+    fk = wl.fit["kind"]
+    f = matfun.f_scalar(fk, lam, tuple(wl.fit.get("params", ())))
+    ii, jj = pairs[:, 0], pairs[:, 1]
+
+    n = M.shape[0]
+
+    def elems(d):
+        # U diag(d) U^T at the pairs: whole matrix when most elements are tracked,
+        # else row pairs in chunks of ~64 MB
+        if len(ii) * 8 > n * n:
+            return ((U * d[None, :]) @ U.T)[ii, jj]
+        out = np.empty(len(ii))
+        ch = max(1, (1 << 23) // n)
+        for c0 in range(0, len(ii), ch):
+            a, b = ii[c0:c0 + ch], jj[c0:c0 + ch]
+            out[c0:c0 + len(a)] = np.einsum("kj,kj->k", U[a] * d[None, :], U[b])
+        return out
+
+    G, GM, F = elems(g), elems(gm), elems(f)
+    ng = float(np.linalg.norm(G))
+    diag = ii == jj
+    sig = float(np.linalg.norm(errs)) / ng
+    sig_d = float(np.linalg.norm(errs[diag]) / np.linalg.norm(G[diag])) if diag.any() else None
+    t_all = steps * (sig / 1e-3) ** 2
+    out = {
+        "eigh_s": t_eigh, "total_s": time.perf_counter() - t0, "steps": steps,
+        "rel_err": float(np.linalg.norm(vals - GM)) / ng, "sigma_rel": sig,
+        "transient": float(np.linalg.norm(GM - G)) / ng,
+        "fit_bias": float(np.linalg.norm(G - F) / np.linalg.norm(F)),
+        "time_to_1e-3_s": t_all * ms_per_step / 1e3, "steps_to_1e-3": t_all,
+    }
+    if sig_d is not None:
+        t_d = steps * (sig_d / 1e-3) ** 2
+        out.update({"sigma_rel_diag": sig_d, "steps_to_1e-3_diag": t_d,
+                    "time_to_1e-3_diag_s": t_d * ms_per_step / 1e3})
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -703,6 +761,7 @@ def main():
     g.run(steps)
     vals, errs = g.elements(pairs)
     t_e2e = time.perf_counter() - t0
+    info_e2e = g.info()
     if wl.csr is not None:
         h2d = wl.csr[0].nbytes + wl.csr[1].nbytes + wl.csr[2].nbytes + pairs.nbytes
     elif wl.precision == "fp64":
@@ -744,6 +803,8 @@ def main():
                                 "shared memory for the whole segment; no HBM traffic per step")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"]["exact"] = exact_target(wl, pairs, vals, errs,
+                                                     int(info_e2e["accumulated"]), ms / steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -177,7 +177,8 @@ enum fth_kernel_class {
     FTH_K_SYRK_TC = 6,      /* tcgen05 all-elements accumulation pass            */
     FTH_K_FLUSH = 7,        /* FP64 block flush                                  */
     FTH_K_FP64_DENSE = 8,   /* FP64 one-CTA-per-replica segment                  */
-    FTH_K_CLASSES = 9
+    FTH_K_FP64_NOISE = 9,   /* FP64 normals of a segment, generated ahead        */
+    FTH_K_CLASSES = 10
 };
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel the context launches:

@@ -37,7 +37,7 @@ EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_g
            "fth_server_result", "fth_server_clock", "fth_server_pool", "fth_server_last_error",
            "fth_server_destroy")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
-                  "syrk_tc", "flush", "fp64_dense")
+                  "syrk_tc", "flush", "fp64_dense", "fp64_noise")
 
 
 class FthError(RuntimeError):

@@ -45,6 +45,8 @@ struct Layout {
     size_t off_q0 = 0, off_q1 = 0, off_p = 0, off_s = 0, off_MQ = 0, off_ophi = 0, off_oplo = 0;
     size_t off_ps = 0, off_ps1 = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
     size_t off_gidx = 0, off_gout = 0, off_err = 0;
+    size_t off_xi = 0;       // FP64 path: normals of one segment
+    int64_t xi_chunk = 0;    // kick indices per segment that the buffer holds
     size_t total = 0;
 };
 
@@ -276,6 +278,10 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_q0 = c.take((size_t)L->R * Np * 8);
         L->off_p = c.take((size_t)L->R * Np * 8);
         L->off_s = c.take((size_t)std::max(nsub, 1) * L->R * Np * 8);
+        // normals generated ahead: up to 4096 kick indices, at most ~64 MiB
+        const size_t per = (size_t)L->R * 2 * L->ns * Np * 8;
+        L->xi_chunk = std::max<int64_t>(2, std::min<int64_t>(4096, (int64_t)((size_t(64) << 20) / per)));
+        L->off_xi = c.take(per * (size_t)L->xi_chunk);
     }
     L->off_pairs = c.take((size_t)std::max<int64_t>(ntracked, 1) * 2 * 4);
     if (L->path == kPathDense64) L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * L->R * 8);
@@ -663,13 +669,21 @@ fth_status run_dense64(fth_ctx* c, int64_t steps) {
         } else {
             seg = std::min(seg, c->block - c->inblock);
         }
-        seg = std::min<int64_t>(seg, 1 << 20);
+        seg = std::min<int64_t>(seg, L.xi_chunk - (c->primed ? 0 : 1));
         const uint32_t kappa0 = (uint32_t)(c->primed ? c->t + 1 : c->t);
+        double* xi = reinterpret_cast<double*>(c->ws + L.off_xi);
+        {
+        ProfScope ps(c, FTH_K_FP64_NOISE);
+        FTH_CK(launch_fp64_noise(L.ns, c->g64, L.N, L.Np, L.R, kappa0, seg + (c->primed ? 0 : 1),
+                                 xi, c->stream),
+               "fp64 noise");
+        }
+        ++c->launches;
         {
         ProfScope ps(c, FTH_K_FP64_DENSE);
         FTH_CK(launch_fp64_dense(L.ns, c->g64, L.N, L.Np, L.R, static_cast<const double*>(c->M),
                                  static_cast<double*>(c->q[0]), static_cast<double*>(c->p),
-                                 static_cast<double*>(c->s), kappa0, seg, c->primed,
+                                 static_cast<double*>(c->s), xi, seg, c->primed,
                                  c->observable, c->pairs, L.ntracked,
                                  static_cast<double*>(c->partial), acc_from, c->stream),
                "fp64 dense");

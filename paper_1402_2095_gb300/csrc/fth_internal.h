@@ -99,10 +99,14 @@ __host__ __device__ inline int64_t packed_index(int64_t i, int64_t j, int64_t nb
 cudaError_t launch_round_tf32(float* x, int64_t n, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);
 
-// FP64 small dense path: one CTA per replica runs `nsteps` fused launches.
+// FP64 small dense path: the normals of a segment are generated ahead over the whole
+// GPU (`xi`: [iters][R][2 ns][Np]), then one CTA per replica runs `nsteps` fused
+// launches (plus the prologue when not primed) reading them.
+cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
+                              uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st);
 cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
-                              const double* M, double* q, double* p, double* s, uint32_t kappa0,
-                              int64_t nsteps, int primed_in, int observable,
+                              const double* M, double* q, double* p, double* s,
+                              const double* noise, int64_t nsteps, int primed_in, int observable,
                               const int32_t* pairs, int64_t npairs, double* partial,
                               int64_t acc_from, cudaStream_t st);
 

@@ -18,39 +18,68 @@ __device__ __forceinline__ double open_unit64(uint32_t x) {
     return (double)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-8;
 }
 
+// Box-Muller in FP64 on one uint32 pair: rho = sqrt(-2 ln u_a), angle 2 pi u_b.
+__device__ __forceinline__ void box_muller64(uint32_t a, uint32_t b, double& z0, double& z1) {
+    const double rho = sqrt(-2.0 * log(open_unit64(a)));
+    double sn, cs;
+    sincospi(2.0 * open_unit64(b), &sn, &cs);
+    z0 = rho * cs;
+    z1 = rho * sn;
+}
+
+// Noise ahead of the integrator: the 2 NS normals of every (kappa, i, r) of a segment of
+// `iters` kick indices from kappa0, written to xi[((it R + r) 2 NS + a) Np + i].  FP64
+// transcendental functions are the bulk of the FP64 path's work; this kernel spreads
+// them over the whole GPU while the integrator (one CTA per replica) stays small.
+// One thread per (it, r, Philox call k, i), i fastest, so the stores coalesce.
 template <int NS>
-__device__ __forceinline__ void gle_normals64(uint32_t kappa, uint32_t i, uint32_t r,
-                                              uint32_t k0, uint32_t k1, double (&xi)[2 * NS]) {
+__global__ void __launch_bounds__(256)
+fp64_noise_kernel(uint32_t key0, uint32_t key1, uint32_t roff, int N, int Np, int R,
+                  uint32_t kappa0, int iters, double* __restrict__ xi) {
     constexpr int kCalls = (2 * NS + 3) / 4;
+    const int64_t total = (int64_t)iters * R * kCalls * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        int64_t rest = e / N;
+        const int k = (int)(rest % kCalls);
+        rest /= kCalls;
+        const int r = (int)(rest % R);
+        const int it = (int)(rest / R);
+        const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i,
+                                                 (uint32_t)r + roff, (uint32_t)k), key0, key1);
+        double* out = xi + ((int64_t)it * R + r) * (2 * NS) * Np + i;
+        double z[4];
+        box_muller64(x.x, x.y, z[0], z[1]);
+        if (4 * k + 2 < 2 * NS) box_muller64(x.z, x.w, z[2], z[3]);
 #pragma unroll
-    for (int k = 0; k < kCalls; ++k) {
-        const uint4 x = philox4x32_10(make_uint4(kappa, i, r, (uint32_t)k), k0, k1);
-        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const double rho = sqrt(-2.0 * log(open_unit64(w[2 * h])));
-            double sn, cs;
-            sincospi(2.0 * open_unit64(w[2 * h + 1]), &sn, &cs);
-            if (4 * k + 2 * h < 2 * NS) xi[4 * k + 2 * h] = rho * cs;
-            if (4 * k + 2 * h + 1 < 2 * NS) xi[4 * k + 2 * h + 1] = rho * sn;
-        }
+        for (int j = 0; j < 4; ++j)
+            if (4 * k + j < 2 * NS) out[(int64_t)(4 * k + j) * Np] = z[j];
     }
 }
 
+// Shared memory: q and the sample x ([Np] each); when they fit, M transposed
+// ([N][Np], so a warp's row reads are conflict-free), the tracked pairs and their
+// per-replica partial sums (written back at the end of the segment).
 template <int NS>
 __global__ void __launch_bounds__(1024)
 fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double* __restrict__ q,
-                  double* __restrict__ p, double* __restrict__ s, uint32_t kappa0, int iters,
-                  int prologue, int observable, const int32_t* __restrict__ pairs, int npairs,
-                  double* __restrict__ partial, int acc_from) {
+                  double* __restrict__ p, double* __restrict__ s, const double* __restrict__ noise,
+                  int iters, int prologue, int observable, const int32_t* __restrict__ pairs,
+                  int npairs, double* __restrict__ partial, int acc_from, int m_smem,
+                  int p_smem) {
     extern __shared__ double sh[];
-    double* qs = sh;        // [Np]
-    double* xs = sh + Np;   // [Np]
+    double* qs = sh;                          // [Np]
+    double* xs = sh + Np;                     // [Np]
+    double* mt = xs + Np;                     // [N][Np] when m_smem
+    double* pacc = mt + (m_smem ? (int64_t)N * Np : 0);             // [npairs] when p_smem
+    int32_t* pidx = reinterpret_cast<int32_t*>(pacc + (p_smem ? npairs : 0));
     const int r = blockIdx.x;
     const int i = threadIdx.x;
     const int R = gridDim.x;
     const int64_t base = (int64_t)r * Np;
     const int64_t plane = (int64_t)R * Np;
+    double* gacc = partial + (int64_t)r * npairs;
     double v[NS];
     double qi = 0.0;
     if (i < N) {
@@ -60,20 +89,53 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         for (int a = 1; a < NS; ++a) v[a] = s[(a - 1) * plane + base + i];
     }
     for (int k = i; k < Np; k += blockDim.x) qs[k] = (k < N) ? q[base + k] : 0.0;
+    if (m_smem)
+        for (int e = i; e < N * N; e += blockDim.x) {
+            const int row = e / N, k = e % N;
+            mt[(int64_t)k * Np + row] = M[(int64_t)row * Np + k];
+        }
+    if (p_smem)
+        for (int e = i; e < npairs; e += blockDim.x) {
+            pacc[e] = gacc[e];
+            pidx[2 * e] = pairs[2 * e];
+            pidx[2 * e + 1] = pairs[2 * e + 1];
+        }
     __syncthreads();
-    double* acc = partial + (int64_t)r * npairs;
+    double* acc = p_smem ? pacc : gacc;
+    const int32_t* pr = p_smem ? pidx : pairs;
     for (int it = 0; it < iters; ++it) {
         const bool pro = prologue && it == 0;
-        const uint32_t kappa = kappa0 + (uint32_t)it;
         double mq = 0.0;
         if (i < N) {
-            const double* mi = M + (int64_t)i * Np;
-            for (int k = 0; k < N; ++k) mq = fma(mi[k], qs[k], mq);
+            // four independent partial sums: the FP64 latency chain is a quarter as long
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int k = 0;
+            if (m_smem) {
+                for (; k + 4 <= N; k += 4) {
+                    a0 = fma(mt[(int64_t)k * Np + i], qs[k], a0);
+                    a1 = fma(mt[(int64_t)(k + 1) * Np + i], qs[k + 1], a1);
+                    a2 = fma(mt[(int64_t)(k + 2) * Np + i], qs[k + 2], a2);
+                    a3 = fma(mt[(int64_t)(k + 3) * Np + i], qs[k + 3], a3);
+                }
+                for (; k < N; ++k) a0 = fma(mt[(int64_t)k * Np + i], qs[k], a0);
+            } else {
+                const double* mi = M + (int64_t)i * Np;
+                for (; k + 4 <= N; k += 4) {
+                    a0 = fma(mi[k], qs[k], a0);
+                    a1 = fma(mi[k + 1], qs[k + 1], a1);
+                    a2 = fma(mi[k + 2], qs[k + 2], a2);
+                    a3 = fma(mi[k + 3], qs[k + 3], a3);
+                }
+                for (; k < N; ++k) a0 = fma(mi[k], qs[k], a0);
+            }
+            mq = (a0 + a1) + (a2 + a3);
         }
         __syncthreads();   // all reads of qs done before it is overwritten
         if (i < N) {
             double xi[2 * NS];
-            gle_normals64<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.key0, g.key1, xi);
+            const double* nz = noise + ((int64_t)it * R + r) * (2 * NS) * Np + i;
+#pragma unroll
+            for (int a = 0; a < 2 * NS; ++a) xi[a] = nz[(int64_t)a * Np];
             if (!pro) {
                 v[0] = fma(-g.hdt, mq, v[0]);
                 o_half<NS, double>(v, g.T, g.S, xi);
@@ -88,9 +150,13 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         const int f = prologue ? it - 1 : it;   // index of this fused launch in the segment
         if (!pro && f >= acc_from) {
             for (int e = i; e < npairs; e += blockDim.x)
-                acc[e] = fma(xs[pairs[2 * e]], xs[pairs[2 * e + 1]], acc[e]);
+                acc[e] = fma(xs[pr[2 * e]], xs[pr[2 * e + 1]], acc[e]);
         }
         // xs is rewritten only after the next iteration's barrier
+    }
+    if (p_smem) {
+        __syncthreads();
+        for (int e = i; e < npairs; e += blockDim.x) gacc[e] = pacc[e];
     }
     if (i < N) {
         q[base + i] = qi;
@@ -100,22 +166,54 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
     }
 }
 
+cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
+                              uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st) {
+    if (iters <= 0) return cudaSuccess;
+    const int64_t calls = (2 * ns + 3) / 4;
+    const int64_t total = iters * R * calls * N;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+#define FTH_F64N_CASE(NSV)                                                                  \
+    case NSV:                                                                               \
+        fp64_noise_kernel<NSV><<<grid, 256, 0, st>>>(g.key0, g.key1, g.roff, (int)N, (int)Np, \
+                                                     (int)R, kappa0, (int)iters, xi);       \
+        break;
+    switch (ns) {
+        FTH_F64N_CASE(1)
+        FTH_F64N_CASE(2)
+        FTH_F64N_CASE(3)
+        FTH_F64N_CASE(4)
+        FTH_F64N_CASE(5)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FTH_F64N_CASE
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
-                              const double* M, double* q, double* p, double* s, uint32_t kappa0,
-                              int64_t nsteps, int primed_in, int observable,
+                              const double* M, double* q, double* p, double* s,
+                              const double* noise, int64_t nsteps, int primed_in, int observable,
                               const int32_t* pairs, int64_t npairs, double* partial,
                               int64_t acc_from, cudaStream_t st) {
     const int prologue = primed_in ? 0 : 1;
     const int iters = (int)nsteps + prologue;
     if (iters <= 0) return cudaSuccess;
     const int threads = (int)std::max<int64_t>(32, ((N + 31) / 32) * 32);
-    const size_t shmem = sizeof(double) * 2 * (size_t)Np;
-    // kappa0 is the kick index of the first iteration (the prologue's when unprimed)
+    // shared memory: q and x always; then the pairs (16 B each) and M when they fit
+    constexpr size_t kBudget = 200 * 1024;
+    size_t shmem = sizeof(double) * 2 * (size_t)Np;
+    const size_t pbytes = (size_t)npairs * 16, mbytes = (size_t)N * Np * 8;
+    const int p_smem = shmem + pbytes <= kBudget ? 1 : 0;
+    if (p_smem) shmem += pbytes;
+    const int m_smem = shmem + mbytes <= kBudget ? 1 : 0;
+    if (m_smem) shmem += mbytes;
+    // noise holds the normals of the segment's kick indices (the prologue's first)
 #define FTH_F64_CASE(NSV)                                                                   \
     case NSV:                                                                               \
+        cudaFuncSetAttribute(fp64_dense_kernel<NSV>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);    \
         fp64_dense_kernel<NSV><<<(unsigned)R, threads, shmem, st>>>(                        \
-            g, (int)N, (int)Np, M, q, p, s, kappa0, iters, prologue, observable, pairs,     \
-            (int)npairs, partial, (int)acc_from);                                           \
+            g, (int)N, (int)Np, M, q, p, s, noise, iters, prologue, observable, pairs,      \
+            (int)npairs, partial, (int)acc_from, m_smem, p_smem);                           \
         break;
     switch (ns) {
         FTH_F64_CASE(1)

@@ -611,9 +611,10 @@ cudaError_t launch_pool_convert(const void* src, int f64, int n, int np, int r0,
 // descriptor, after a fence) advances the problem's counters and, at a block end,
 // folds the block means into the FP64 Welford sums.  A prologue launch only marks the
 // problem primed.
+template <int RN>
 __global__ void __launch_bounds__(256)
 pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ items, int nitems,
-                  int RN, uint32_t* err) {
+                  uint32_t* err) {
     __shared__ int s_last, s_flush;
     __shared__ double s_nb;
     for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
@@ -625,16 +626,26 @@ pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ i
             const float4* a = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e] * RN);
             const float4* b = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e + 1] * RN);
             float acc0 = 0.f, acc1 = 0.f;
-            for (int r = 0; r < RN / 4; r += 2) {
-                const float4 u0 = a[r], v0 = b[r], u1 = a[r + 1], v1 = b[r + 1];
-                acc0 = fmaf(u0.x, v0.x, acc0);
-                acc1 = fmaf(u1.x, v1.x, acc1);
-                acc0 = fmaf(u0.y, v0.y, acc0);
-                acc1 = fmaf(u1.y, v1.y, acc1);
-                acc0 = fmaf(u0.z, v0.z, acc0);
-                acc1 = fmaf(u1.z, v1.z, acc1);
-                acc0 = fmaf(u0.w, v0.w, acc0);
-                acc1 = fmaf(u1.w, v1.w, acc1);
+            // rows of 32 replicas: all 16 loads of a chunk in flight before the FMAs
+#pragma unroll
+            for (int r0 = 0; r0 < RN / 4; r0 += 8) {
+                float4 u[8], v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    u[k] = a[r0 + k];
+                    v[k] = b[r0 + k];
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    acc0 = fmaf(u[k].x, v[k].x, acc0);
+                    acc1 = fmaf(u[k + 1].x, v[k + 1].x, acc1);
+                    acc0 = fmaf(u[k].y, v[k].y, acc0);
+                    acc1 = fmaf(u[k + 1].y, v[k + 1].y, acc1);
+                    acc0 = fmaf(u[k].z, v[k].z, acc0);
+                    acc1 = fmaf(u[k + 1].z, v[k + 1].z, acc1);
+                    acc0 = fmaf(u[k].w, v[k].w, acc0);
+                    acc1 = fmaf(u[k + 1].w, v[k + 1].w, acc1);
+                }
             }
             d.partial[e] += acc0 + acc1;
         }
@@ -690,7 +701,13 @@ pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ i
 cudaError_t launch_pool_accum(PoolDesc* desc, const PoolAccItem* items, int nitems, int RN,
                               uint32_t* err, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    pool_accum_kernel<<<std::min(nitems, 152 * 8), 256, 0, st>>>(desc, items, nitems, RN, err);
+    const int grid = std::min(nitems, 152 * 8);
+    switch (RN) {
+        case 32: pool_accum_kernel<32><<<grid, 256, 0, st>>>(desc, items, nitems, err); break;
+        case 64: pool_accum_kernel<64><<<grid, 256, 0, st>>>(desc, items, nitems, err); break;
+        case 128: pool_accum_kernel<128><<<grid, 256, 0, st>>>(desc, items, nitems, err); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
