@@ -420,13 +420,14 @@ class Ragged:
 
     def work(self, cls):
         """Algorithmic bytes per launch of each pool kernel class (all HBM-bound):
-        force: M as BF16 hi+lo (4 B per element), q^T operand hi+lo in, M q out;
+        force: the N(N+1)/2 distinct elements of the symmetric M as BF16 hi+lo (4 B each),
+        q^T operand hi+lo in, M q out;
         gle: 60 B per (i, r) (q, p, s1..s4, M q in; q, p, s1..s4, sample, operand out);
         accumulate: the sample rows of every tracked pair."""
         N = self.sizes.astype(np.float64)
         R = self.R
         if cls == "pool_force":
-            return float(np.sum(4.0 * N * N + 4.0 * N * R + 4.0 * N * R))
+            return float(np.sum(2.0 * N * (N + 1) + 4.0 * N * R + 4.0 * N * R))
         if cls == "pool_gle":
             return float(np.sum(60.0 * N * R))
         if cls == "pool_accum":
@@ -506,8 +507,9 @@ def run_ragged(args, rank, world, local):
                    "tuned_grid": st["tuned_grid"], "tuned_force_us": st["tuned_us"],
                    "gle_variant": st["gle_variant"], "tuned_gle_us": st["gle_us"],
                    "parallelism": f"replicas x{world}",
-                   "l2": "per-step working set (M hi+lo %.0f MB + state) > L2; steps back to back"
-                         % (wl.work("pool_force") / 1e6)},
+                   "l2": "per-step working set (M hi+lo upper blocks %.0f MB + state %.0f MB) > L2; "
+                         "steps back to back" % (wl.work("pool_force") / 1e6,
+                                                 wl.work("pool_gle") / 1e6)},
         "gpu_launches": 3 * steps,
         "clocks": clk,
         "roofline": roof,

@@ -39,10 +39,13 @@ Layout problem_layout(int kind, int64_t n, int64_t nnz, int ns, int64_t R, int p
     };
     const size_t plane = (size_t)n * R * 4;
     if (kind == FTH_DENSE) {
-        const int64_t np = rup(n, 128);
+        const int64_t np = rup(n, 128), nb = np / 128;
         const size_t esz = prec == FTH_PREC_TF32 ? 4 : 2;
-        L.a_hi = take((size_t)np * np * esz);
-        if (prec == FTH_PREC_BF16X3) L.a_lo = take((size_t)np * np * esz);
+        // BF16X3 stores the upper 128 x 128 blocks only (32 KiB each per plane)
+        const size_t mbytes = prec == FTH_PREC_BF16X3 ? (size_t)(nb * (nb + 1) / 2) * 32768
+                                                      : (size_t)np * np * esz;
+        L.a_hi = take(mbytes);
+        if (prec == FTH_PREC_BF16X3) L.a_lo = take(mbytes);
         L.bt_hi = take((size_t)np * R * esz);
         if (prec == FTH_PREC_BF16X3) L.bt_lo = take((size_t)np * R * esz);
         L.mq = take(plane);
@@ -486,6 +489,7 @@ fth_status fth_pool_add(fth_pool* P, const fth_matrix* M, const fth_gle* gle,
     d.observable = po->observable;
     d.npairs = (int)po->npairs;
     d.live = 1;
+    d.sym = (M->kind == FTH_DENSE && P->prec == FTH_PREC_BF16X3) ? 1 : 0;
     d.burnin = po->burnin;
     d.block = po->block;
     d.mq = L.mq ? reinterpret_cast<float*>(base + L.mq) : nullptr;

@@ -18,10 +18,14 @@ struct PoolDesc {
     int observable;
     int npairs;
     int live;
-    int pad0;
+    int sym;                // dense BF16: M stored as its upper 128 x 128 blocks only
     int64_t burnin, block;
-    // dense force operands: M blocked and pre-swizzled in 128-byte K slices
-    // ([n/128][np/KS][128][128 B]), q^T slices ([np/KS][R][128 B])
+    // dense force operands.  TF32: M blocked and pre-swizzled in 128-byte K slices
+    // ([np/128][np/32][128][128 B]).  BF16 (sym): the upper blocks (I <= J) in packed
+    // order, each as four 64 x 64 sub-tiles (row half a, column half b) at
+    // (2 b + a) * 8 KiB, 128-byte rows, 16-byte chunk c of row r at c ^ (r & 7); a lower
+    // block is read as the transpose of its mirror (MN-major A operand).
+    // q^T slices ([np/KS][R][128 B]).
     uint8_t* a_hi;
     uint8_t* a_lo;
     uint8_t* bt_hi;

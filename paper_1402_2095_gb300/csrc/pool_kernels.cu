@@ -88,20 +88,40 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
             const PoolForceItem it = items[j];
             const PoolDesc& d = desc[it.problem];
             const int nk = d.np / KS;
-            const uint8_t* a_hi = d.a_hi + (size_t)it.rb * nk * C::kABytes;
-            const uint8_t* a_lo = d.a_lo + (size_t)it.rb * nk * C::kABytes;
+            const int J = it.rb, nb = d.np >> 7;
+            const bool sym = KIND == 2 && d.sym;
             for (int kb = 0; kb < nk && ok; ++kb, ++c) {
                 const int st = c % STAGES;
                 if (c >= STAGES) ok = mbar_wait(&empty[st], ((c / STAGES) + 1) & 1, err);
                 if (!ok) break;
                 uint8_t* base = stages + st * C::kStageBytes;
                 mbar_expect_tx(&full[st], C::kStageBytes);
-                bulk_load(base, a_hi + (size_t)kb * C::kABytes, C::kABytes, &full[st]);
-                bulk_load(base + C::kABytes, d.bt_hi + (size_t)kb * C::kBBytes, C::kBBytes, &full[st]);
-                if (KIND == 2) {
-                    bulk_load(base + C::kABytes + C::kBBytes, a_lo + (size_t)kb * C::kABytes,
-                              C::kABytes, &full[st]);
-                    bulk_load(base + 2 * C::kABytes + C::kBBytes, d.bt_lo + (size_t)kb * C::kBBytes,
+                // A slice: byte offset within a plane, and whether it is the mirror's
+                // transpose (two 8 KiB sub-tiles) or a plain K-major slice (16 KiB)
+                size_t a_off;
+                bool mn = false;
+                if (sym) {
+                    const int cb = kb >> 1, h = kb & 1;
+                    if (cb >= J) {
+                        a_off = (size_t)(J * nb - J * (J - 1) / 2 + (cb - J)) * 32768 + h * 16384;
+                    } else {
+                        a_off = (size_t)(cb * nb - cb * (cb - 1) / 2 + (J - cb)) * 32768 + h * 8192;
+                        mn = true;
+                    }
+                } else {
+                    a_off = ((size_t)J * nk + kb) * C::kABytes;
+                }
+                const int nplanes = KIND == 2 ? 2 : 1;
+                for (int pl = 0; pl < nplanes; ++pl) {
+                    const uint8_t* a = (pl ? d.a_lo : d.a_hi) + a_off;
+                    uint8_t* sa = base + pl * (C::kABytes + C::kBBytes);
+                    if (mn) {
+                        bulk_load(sa, a, 8192, &full[st]);
+                        bulk_load(sa + 8192, a + 16384, 8192, &full[st]);
+                    } else {
+                        bulk_load(sa, a, C::kABytes, &full[st]);
+                    }
+                    bulk_load(sa + C::kABytes, (pl ? d.bt_lo : d.bt_hi) + (size_t)kb * C::kBBytes,
                               C::kBBytes, &full[st]);
                 }
             }
@@ -123,7 +143,9 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
             if (!ok) break;
             fence_after_sync();
             const PoolForceItem it = items[j];
-            const int nk = desc[it.problem].np / KS;
+            const PoolDesc& d = desc[it.problem];
+            const int nk = d.np / KS;
+            const bool sym = KIND == 2 && d.sym;
             const uint32_t acc_t = tmem + (uint32_t)(a * RN);
             for (int kb = 0; kb < nk; ++kb, ++c) {
                 const int st = c % STAGES;
@@ -132,21 +154,27 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
                     break;
                 }
                 fence_after_sync();
+                const bool mn = sym && (kb >> 1) < it.rb;
                 const uint32_t base = smem_u32(stages + st * C::kStageBytes);
-                const uint64_t ah = sw128_desc(base);
+                const uint32_t abase_lo = base + C::kABytes + C::kBBytes;
+                // K-major A advances 32 bytes per MMA (16 BF16 / 8 TF32 of K within the
+                // swizzled row); MN-major A advances two 8-row K groups (2048 bytes)
+                const uint64_t ah = mn ? sw128_mn_desc(base, 8192) : sw128_desc(base);
+                const uint64_t al = mn ? sw128_mn_desc(abase_lo, 8192) : sw128_desc(abase_lo);
                 const uint64_t bh = sw128_desc(base + C::kABytes);
+                const uint32_t id = mn ? (idesc | (1u << 15)) : idesc;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                    const uint64_t adv_b = (uint64_t)((kk * 32) >> 4);
+                    const uint64_t adv_a = mn ? (uint64_t)((kk * 2048) >> 4) : adv_b;
                     const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                     if (KIND == 1) {
-                        umma<1>(acc_t, ah + adv, bh + adv, idesc, acc);
+                        umma<1>(acc_t, ah + adv_a, bh + adv_b, id, acc);
                     } else {
-                        const uint64_t al = sw128_desc(base + C::kABytes + C::kBBytes);
                         const uint64_t bl = sw128_desc(base + 2 * C::kABytes + C::kBBytes);
-                        umma<2>(acc_t, al + adv, bh + adv, idesc, acc);
-                        umma<2>(acc_t, ah + adv, bl + adv, idesc, 1u);
-                        umma<2>(acc_t, ah + adv, bh + adv, idesc, 1u);
+                        umma<2>(acc_t, al + adv_a, bh + adv_b, id, acc);
+                        umma<2>(acc_t, ah + adv_a, bl + adv_b, id, 1u);
+                        umma<2>(acc_t, ah + adv_a, bh + adv_b, id, 1u);
                     }
                 }
                 umma_commit(&empty[st]);
@@ -567,11 +595,12 @@ cudaError_t launch_pool_progress(const PoolDesc* desc, const int* live, int nliv
 
 // ------------------------------------------------------------------ operand conversion
 // Rows [r0, r0 + nr) of a dense matrix (row-major, n columns, FP32 or FP64 at `src`,
-// whose row 0 is row r0) into the force operand layout: element (i, k) at byte
-// ((i / 128 * (np / KS) + k / KS) * 128 + i % 128) * 128 + swizzled column, where the
-// 16-byte chunk c of row r sits at chunk position c ^ (r & 7).  BF16X3 (kind 2) stores
-// hi = bf16(x) and lo = bf16(x - hi), both round-to-nearest-even; TF32 (kind 1) stores
-// x rounded to nearest (ties away), as the tensor core reads it.
+// whose row 0 is row r0) into the force operand layout.  TF32 (kind 1): element (i, k)
+// at byte ((i / 128 * (np / 32) + k / 32) * 128 + i % 128) * 128 + swizzled column, x
+// rounded to nearest (ties away) as the tensor core reads it.  BF16X3 (kind 2): the
+// upper 128 x 128 blocks only (M is symmetric, Eq. 5), each as four 64 x 64 sub-tiles
+// (see PoolDesc), hi = bf16(x) and lo = bf16(x - hi), round-to-nearest-even.  In every
+// layout the 16-byte chunk c of a 128-byte row r sits at chunk position c ^ (r & 7).
 __global__ void pool_convert_kernel(const void* __restrict__ src, int f64, int n, int np,
                                     int r0, int nr, int kind, uint8_t* __restrict__ a_hi,
                                     uint8_t* __restrict__ a_lo) {
@@ -582,9 +611,21 @@ __global__ void pool_convert_kernel(const void* __restrict__ src, int f64, int n
         const int64_t i = r0 + e / n, k = e % n;
         const float x = f64 ? (float)static_cast<const double*>(src)[e]
                             : static_cast<const float*>(src)[e];
-        const int64_t r = i & 127, col = (k % ks) * esz;
-        const size_t o = (size_t)((((i >> 7) * (np / ks) + k / ks) * 128 + r) * 128 +
-                                  ((((col >> 4) ^ (r & 7)) << 4) | (col & 15)));
+        size_t o;
+        if (kind == 1) {
+            const int64_t r = i & 127, col = (k % ks) * esz;
+            o = (size_t)((((i >> 7) * (np / ks) + k / ks) * 128 + r) * 128 +
+                         ((((col >> 4) ^ (r & 7)) << 4) | (col & 15)));
+        } else {
+            // upper blocks only; a lower block is never stored (the mirror serves it)
+            const int64_t I = i >> 7, J = k >> 7, nb = np >> 7;
+            if (I > J) continue;
+            const int64_t r = i & 127, cc = k & 127;
+            const int64_t rr = r & 63, col = (cc & 63) * 2;
+            o = (size_t)((I * nb - I * (I - 1) / 2 + (J - I)) * 32768 +
+                         ((cc >> 6) * 2 + (r >> 6)) * 8192 + rr * 128 +
+                         ((((col >> 4) ^ (rr & 7)) << 4) | (col & 15)));
+        }
         if (kind == 1) {
             *reinterpret_cast<float*>(a_hi + o) = to_tf32_pool(x);
         } else {

@@ -97,6 +97,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor: MN-major, SWIZZLE_128B.  Atoms of 64 16-bit MN
+// elements (128 B) x 8 K rows (1024 B); `lbo` bytes between atoms along MN, 1024 bytes
+// between 8-row groups along K.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;   // leading byte offset: next MN atom
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8 K rows
+    d |= (uint64_t)1 << 46;                         // descriptor version
+    d |= (uint64_t)2 << 61;                         // swizzle mode: 128B
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = BN.
 // ab_fmt: 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
 __host__ __device__ constexpr uint32_t make_idesc(int ab_fmt, int n) {
