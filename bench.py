@@ -91,8 +91,69 @@ class Workload:
             self.label = ("64^3 periodic lattice CSR (N=262144, 7-point), Fermi beta=2 mu=7, "
                           "R=64, diagonal + nearest-neighbour elements")
             self.default_steps, self.cpu_replicas = 2000, 4
+        elif name == "m1":
+            # the paper's logarithm benchmark: Tr ln M1 (Appendix M1: n^3 lattice, on-site
+            # 100, hopping U[0,2] to six neighbour shells), ln fitted on [e, 100e], M1
+            # scaled into it: Tr ln M1 = Tr ln(r M1) - N ln r
+            import scipy.sparse as sp
+            import scipy.sparse.linalg as spla
+            n1 = 16
+            self.n, self.R, self.block = n1 ** 3, 64, 1000
+            self.seed = syn.BASE_SEED + 5
+            rowptr, col, val = syn.m1_csr(n1, seed=self.seed)
+            A = sp.csr_matrix((val, col, rowptr), shape=(self.n, self.n))
+            lo = float(spla.eigsh(A, k=1, which="SA", return_eigenvectors=False, tol=1e-8)[0])
+            hi = float(spla.eigsh(A, k=1, which="LA", return_eigenvectors=False, tol=1e-8)[0])
+            self.spectrum = (lo, hi)
+            self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("log_e_100e")
+            self.r = float(np.e) * 1.0005 / lo             # r lo just above e
+            if self.r * hi > 100 * np.e:
+                raise ValueError("M1 spectrum wider than the fitted range")
+            self.csr = (rowptr, col, (self.r * val).astype(np.float32), self.n)
+            self.nnz = len(col)
+            self.mu = None
+            self.precision = "fp32"
+            self.track, self.pairs = "diag", syn.diag_pairs(self.n)
+            self.trace = ("log", self.r)
+            self.label = (f"Tr ln M1, M1 = paper's Appendix lattice n={n1} (N={self.n}, 80 "
+                          f"neighbours), ln fitted on [e,100e], r={self.r:.5f}, R=64, diagonal")
+            self.default_steps, self.cpu_replicas = 20000, 4
+        elif name == "m2":
+            # the paper's exponential benchmark: Tr exp(-M2/100) (Appendix M2, eigenvalues
+            # in (-300, 300)); exp(-x/100) fitted on [1, 601] for M2 + 301 I
+            m = 2048
+            self.n, self.R, self.block = m, 256, 1000
+            self.seed = syn.BASE_SEED + 6
+            M2 = syn.m2_dense(m, seed=self.seed)
+            self.shift = 301.0
+            self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("exp_001_1_601")
+            self.M32 = (M2 + self.shift * np.eye(m)).astype(np.float32)
+            self.mu = None
+            self.precision = precision
+            self.track, self.pairs = "diag", syn.diag_pairs(m)
+            self.trace = ("exp", 0.01, self.shift)
+            self.label = (f"Tr exp(-M2/100), M2 = paper's Appendix dense random (m={m}, "
+                          f"eigenvalues in (-300,300)) + 301 I, exp(-x/100) fitted on [1,601], "
+                          f"R=256, diagonal")
+            self.default_steps, self.cpu_replicas = 20000, 8
         else:
             raise ValueError(name)
+        if not hasattr(self, "trace"):
+            self.trace = None
+
+    def untransform(self, v):
+        """The wanted trace from the sampled one (paper's inverse transforms)."""
+        from paper_1402_2095_gb300 import transforms as tr
+        if self.trace is None:
+            return v
+        if self.trace[0] == "log":
+            return tr.log_trace_from_scaled(v, self.n, self.trace[1])
+        return float(tr.exp_from_shifted(v, self.trace[1], self.trace[2]))
+
+    def untransform_err(self, e):
+        if self.trace is None or self.trace[0] == "log":
+            return e
+        return float(e * np.exp(self.trace[1] * self.trace[2]))
 
     def matrix_kwargs(self, device, pinned=False):
         import torch
@@ -277,7 +338,7 @@ def cpu_baseline(wl, budget_s=CPU_BUDGET_S):
                       f"{steps} steps in {el:.1f} s"}
 
 
-def exact_target(wl, pairs, vals, errs, steps, ms_per_step):
+def exact_target(wl, pairs, vals, errs, steps, ms_per_step, trace_est=None):
     """Part of the CPU baseline: the oracle's exact route (FP64 eigendecomposition, per-mode
     discrete response of the fitted GLE), timed, and the GPU estimate's error against it.
 
@@ -286,11 +347,17 @@ def exact_target(wl, pairs, vals, errs, steps, ms_per_step):
     the block error bars; time_to_1e-3: steps x (sigma_rel / 1e-3)^2 x the GPU step time
     (the statistical error falls as steps^-1/2); transient: ||E[est] - g|| / ||g||;
     fit_bias: ||g - f|| / ||f|| (the fitted GLE against the wanted function)."""
-    if wl.csr is not None:
+    if wl.csr is not None and wl.n > 8192:
         return {"skipped": "the exact lattice target needs a Chebyshev expansion per tracked "
                            "element (1,048,576 of them): beyond the baseline's time budget"}
     from oracle import gle, matfun
-    M = wl.oracle_matrix()["M"]
+    om = wl.oracle_matrix()
+    if "M" in om:
+        M = om["M"]
+    else:
+        import scipy.sparse as sp
+        rowptr, col, val, n_ = om["csr"]
+        M = sp.csr_matrix((val, col, rowptr), shape=(n_, n_)).toarray()
     t0 = time.perf_counter()
     lam, U = np.linalg.eigh(M)
     t_eigh = time.perf_counter() - t0
@@ -332,6 +399,17 @@ def exact_target(wl, pairs, vals, errs, steps, ms_per_step):
         t_d = steps * (sig_d / 1e-3) ** 2
         out.update({"sigma_rel_diag": sig_d, "steps_to_1e-3_diag": t_d,
                     "time_to_1e-3_diag_s": t_d * ms_per_step / 1e3})
+    if trace_est is not None:
+        # the paper's own benchmark quantity: the trace, against its exact value
+        tr_g, tr_gm, tr_f = float(np.sum(g)), float(np.sum(gm)), float(np.sum(f))
+        sig_t = trace_est[1] / abs(tr_g)
+        t_t = steps * (sig_t / 1e-3) ** 2
+        out["trace"] = {
+            "sampled": trace_est[0], "errbar": trace_est[1], "exact_expected": tr_gm,
+            "exact_g": tr_g, "exact_f": tr_f,
+            "rel_err": abs(trace_est[0] - tr_gm) / abs(tr_g), "sigma_rel": sig_t,
+            "wanted": wl.untransform(trace_est[0]), "wanted_exact": wl.untransform(tr_f),
+            "steps_to_1e-3": t_t, "time_to_1e-3_s": t_t * ms_per_step / 1e3}
     return out
 
 
@@ -681,7 +759,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense4096",
-                    choices=["dense4096", "small_fp64", "lattice64", "ragged512", "serving"])
+                    choices=["dense4096", "small_fp64", "lattice64", "ragged512", "serving", "m1",
+                             "m2"])
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--window", type=float, default=1.0, help="serving: arrival window (s)")
     ap.add_argument("--budget", type=int, default=10000, help="serving: step budget per request")
@@ -719,6 +798,9 @@ def main():
                   precision=wl.precision, track=wl.track, pairs=wl.pairs, block=wl.block,
                   stream=stream, replica_offset=rank * wl.R)
     f = FTH(**wl.matrix_kwargs(device=True), **ctx_kw)
+    if wl.trace is not None:
+        from paper_1402_2095_gb300.binding import trace_terms
+        f.add_functional(*trace_terms(n=wl.n))
     f.run(args.warmup)
     torch.cuda.synchronize()
     l0 = f.info()["launches"]
@@ -760,8 +842,10 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = FTH(**wl.matrix_kwargs(device=False, pinned=True), **dict(ctx_kw, seed=wl.seed + 1))
+    gfid = g.add_functional(*trace_terms(n=wl.n)) if wl.trace is not None else None
     g.run(steps)
     vals, errs = g.elements(pairs)
+    trace_est = g.functional(gfid) if gfid is not None else None
     t_e2e = time.perf_counter() - t0
     info_e2e = g.info()
     if wl.csr is not None:
@@ -800,13 +884,24 @@ def main():
                 ((wl.n // 128) * (wl.n // 128 + 1) // 2 * 128 * 128 * 4) >> 20))
     elif wl.name == "lattice64":
         line["config"]["l2"] = "state 805 MB per step > L2 (129 MB); steps back to back"
+    elif wl.name in ("m1", "m2"):
+        planes = (8 if wl.csr is not None else 9) * wl.n * wl.R * 4
+        mbytes = 8 * wl.nnz if wl.csr is not None else wl.M32.nbytes
+        line["config"]["l2"] = ("per-step working set %.0f MB (matrix %.0f MB + state) is below L2 "
+                                "(129 MB): L2-resident by the workload's size, no flush between "
+                                "steps" % ((planes + mbytes) / 1e6, mbytes / 1e6))
     else:
         line["config"]["l2"] = ("whole problem fits on chip (N=32): FP64 state in registers and "
                                 "shared memory for the whole segment; no HBM traffic per step")
+    if trace_est is not None:
+        line["estimate"] = {"sampled_trace": trace_est[0], "sampled_errbar": trace_est[1],
+                            "trace": wl.untransform(trace_est[0]),
+                            "errbar": wl.untransform_err(trace_est[1]), "steps": steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
         line["cpu_baseline"]["exact"] = exact_target(wl, pairs, vals, errs,
-                                                     int(info_e2e["accumulated"]), ms / steps)
+                                                     int(info_e2e["accumulated"]), ms / steps,
+                                                     trace_est)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

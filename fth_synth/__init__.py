@@ -54,6 +54,76 @@ def dense_spd(n: int, lam_lo: float, lam_hi: float, seed: int):
 # ----------------------------------------------------------------------------------
 # Sparse periodic cubic lattices (7-point stencil)
 # ----------------------------------------------------------------------------------
+def shell_offsets(shells: int = 6):
+    """Lattice offsets (dx, dy, dz) of the first `shells` neighbour shells of a simple
+    cubic lattice, by squared distance 1, 2, 3, 4, 5, 6 (6 + 12 + 8 + 6 + 24 + 24 = 80
+    neighbours for six shells), in a fixed order."""
+    out = []
+    r = 3
+    for d2 in range(1, 64):
+        sh = [(x, y, z) for x in range(-r, r + 1) for y in range(-r, r + 1)
+              for z in range(-r, r + 1) if x * x + y * y + z * z == d2]
+        if sh:
+            out.append(sh)
+        if len(out) == shells:
+            break
+    return [o for sh in out for o in sh]
+
+
+def m1_csr(n: int, seed: int, onsite: float = 100.0, hop_hi: float = 2.0, shells: int = 6):
+    """The paper's M1 matrices (Appendix, logarithm example): a periodic n^3 cubic
+    lattice, dof i at site (i / n^2, (i % n^2) / n, i % n); diagonal = the on-site term;
+    hopping uniform in [0, hop_hi] between every pair of sites up to the `shells`-th
+    neighbour shell (periodic distance), one draw per pair (the matrix is symmetric).
+    n >= 7 keeps the 80 neighbours of six shells distinct under periodicity.
+
+    Returns (rowptr int32[N+1], col int32[nnz], val float64[nnz]), columns sorted."""
+    if n < 2 * 3 + 1:
+        raise ValueError("n >= 7 keeps the periodic neighbour shells distinct")
+    g = rng(seed)
+    N = n ** 3
+    idx = np.arange(N, dtype=np.int64)
+    x, y, z = idx // (n * n), (idx % (n * n)) // n, idx % n
+    offs = shell_offsets(shells)
+    half = [o for o in offs if o > (0, 0, 0)]          # one of each +/- pair
+    rows, cols, vals = [idx], [idx], [np.full(N, float(onsite))]
+    for (dx, dy, dz) in half:
+        j = ((x + dx) % n) * n * n + ((y + dy) % n) * n + (z + dz) % n
+        h = g.uniform(0.0, hop_hi, size=N)
+        rows += [idx, j]
+        cols += [j, idx]
+        vals += [h, h]
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals)
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    return np.cumsum(rowptr).astype(np.int32), c.astype(np.int32), v
+
+
+def m2_dense(m: int, seed: int, a: float = -300.0, b: float = 300.0) -> np.ndarray:
+    """The paper's M2 matrices (Appendix, exponential example): diagonal D(i) uniform in
+    [a + (b-a)/4, b - (b-a)/4]; then, row by row (i ascending, j = 0 .. i-1), the element
+    (i, j) = (j, i) is uniform in [-r/(i-j), r/(i-j)] with
+    r = min[D(i)-R(i)-a, b-D(i)-R(i), D(j)-R(j)-a, b-D(j)-R(j)], and both Gerschgorin
+    radii R(i), R(j) grow by its absolute value: every eigenvalue lies in (a, b)."""
+    g = rng(seed)
+    D = g.uniform(a + (b - a) / 4.0, b - (b - a) / 4.0, size=m)
+    R = np.zeros(m)
+    M = np.diag(D)
+    for i in range(1, m):
+        u = g.uniform(-1.0, 1.0, size=i)
+        for j in range(i):
+            r = min(D[i] - R[i] - a, b - D[i] - R[i], D[j] - R[j] - a, b - D[j] - R[j])
+            xv = u[j] * r / (i - j)
+            M[i, j] = M[j, i] = xv
+            R[i] += abs(xv)
+            R[j] += abs(xv)
+    return M
+
+
 def lattice_site(i: int, L: int):
     """Site coordinates of dof i on an L^3 lattice, in the index order of the
     paper's Appendix (x = i / L^2, y = (i % L^2) / L, z = i % L)."""

@@ -148,6 +148,21 @@ fth_status fth_elements(fth_ctx* ctx, const int64_t* pairs, int64_t k, double* v
 
 /* Copy one state plane to / from the host in FP64, layout [R][N] ([R][s][N] for s). */
 fth_status fth_get_state(fth_ctx* ctx, int plane, double* host);
+
+/* Linear functionals of tracked elements, L = sum_k w_k <x_{i_k} x_{j_k}>: the trace
+ * estimators of Sec. "The f-thermostat" -- Tr f(M) = <p^T p> (unit weights on the
+ * diagonal) and Tr O f(M) = <p^T O p> (w = O_ii on (i, i), 2 O_ij on (i < j) for a
+ * symmetric O) -- with their own block error bar: at every block flush the block value
+ * of L is folded into FP64 Welford sums, so correlations between the terms are kept.
+ * Every (i, j) must be tracked (NOT_TRACKED otherwise).  Add before the first sample is
+ * accumulated.  Device storage: `device_buffer` (caller-owned, 256-byte aligned, at
+ * least fth_functional_bytes(nterms) bytes, kept until the context is destroyed). */
+size_t fth_functional_bytes(int64_t nterms);
+fth_status fth_functional_add(fth_ctx* ctx, const int64_t* pairs, const double* weights,
+                              int64_t nterms, void* device_buffer, size_t bytes, int64_t* id);
+/* Value (all accumulated samples, as fth_elements) and block error bar (NaN before two
+ * complete blocks).  Synchronises the stream. */
+fth_status fth_functional(fth_ctx* ctx, int64_t id, double* value, double* errbar);
 fth_status fth_set_state(fth_ctx* ctx, int plane, const double* host);
 
 /* Counters and configuration of a context. */

@@ -35,7 +35,7 @@ EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_g
            "fth_pool_stats", "fth_pool_profile", "fth_pool_progress", "fth_pool_last_error",
            "fth_pool_destroy", "fth_server_create", "fth_server_submit", "fth_server_step",
            "fth_server_result", "fth_server_clock", "fth_server_pool", "fth_server_last_error",
-           "fth_server_destroy")
+           "fth_server_destroy", "fth_functional_bytes", "fth_functional_add", "fth_functional")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense", "fp64_noise")
 
@@ -154,6 +154,9 @@ def load(path: str = LIB_PATH):
         "fth_pool_stats": ([P, P], INT),
         "fth_pool_profile": ([P, I64, P, P], INT),
         "fth_pool_progress": ([P, P, P], INT),
+        "fth_functional_bytes": ([I64], ctypes.c_size_t),
+        "fth_functional_add": ([P, P, P, I64, P, ctypes.c_size_t, P], INT),
+        "fth_functional": ([P, I64, P, P], INT),
         "fth_server_create": ([P, P, ctypes.c_size_t, P], INT),
         "fth_server_submit": ([P, P, P, P, D, I64, P], INT),
         "fth_server_step": ([P, P], INT),
@@ -287,6 +290,7 @@ class FTH:
         _check(L.fth_create(ctypes.byref(mat), ctypes.byref(gle), ctypes.byref(opt),
                             self.workspace.data_ptr(), self.workspace.numel(), ctypes.byref(ctx)))
         self.ctx = ctx
+        self._func_bufs = []
         self._keep_inputs = self._keep  # host copies are only read during create
         self._keep = []
 
@@ -316,6 +320,32 @@ class FTH:
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(shape))
         if a.size:
             _check(load().fth_set_state(self.ctx, PLANE[plane], a.ctypes.data), self.ctx)
+
+    def add_functional(self, pairs, weights):
+        """Register L = sum_k w_k <x_i x_j> over tracked pairs (before the first sample);
+        returns its id.  See trace_terms() for Tr f(M) and Tr O f(M)."""
+        import torch
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+        if w.shape[0] != pr.shape[0]:
+            raise ValueError("one weight per pair")
+        L = load()
+        nbytes = int(L.fth_functional_bytes(pr.shape[0]))
+        with torch.cuda.stream(self.stream):
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        fid = ctypes.c_int64(-1)
+        _check(L.fth_functional_add(self.ctx, pr.ctypes.data, w.ctypes.data, pr.shape[0], ptr,
+                                    nbytes, ctypes.byref(fid)), self.ctx)
+        self._func_bufs.append(buf)
+        return int(fid.value)
+
+    def functional(self, fid):
+        """(value, block error bar) of a registered functional."""
+        v = ctypes.c_double()
+        e = ctypes.c_double()
+        _check(load().fth_functional(self.ctx, int(fid), ctypes.byref(v), ctypes.byref(e)), self.ctx)
+        return v.value, e.value
 
     def info(self) -> dict:
         i = fth_info_t()
@@ -619,3 +649,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------- estimator helpers
+def trace_terms(n=None, O=None):
+    """(pairs, weights) of Tr f(M) = sum_i <p_i p_i> (O None; n = order) or of
+    Tr O f(M) = sum_ij O_ij <p_i p_j> for a symmetric O (dense array or scipy sparse):
+    O_ii on (i, i) and 2 O_ij on (i, j), i < j."""
+    if O is None:
+        idx = np.arange(int(n), dtype=np.int64)
+        return np.stack([idx, idx], axis=1), np.ones(int(n))
+    try:
+        import scipy.sparse as sp
+        if sp.issparse(O):
+            C = sp.triu(sp.coo_matrix(O)).tocoo()
+            i, j, v = C.row.astype(np.int64), C.col.astype(np.int64), C.data.astype(np.float64)
+            w = np.where(i == j, v, 2.0 * v)
+            keep = w != 0
+            return np.stack([i[keep], j[keep]], axis=1), w[keep]
+    except ImportError:
+        pass
+    A = np.asarray(O, dtype=np.float64)
+    i, j = np.triu_indices(A.shape[0])
+    v = A[i, j]
+    w = np.where(i == j, v, 2.0 * v)
+    keep = w != 0
+    return np.stack([i[keep], j[keep]], axis=1).astype(np.int64), w[keep]

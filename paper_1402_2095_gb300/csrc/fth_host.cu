@@ -370,6 +370,16 @@ struct fth_ctx {
     TcSyrk* tcs1 = nullptr;
     // host-side bookkeeping
     std::unordered_map<uint64_t, int64_t> pair_index;
+    // linear functionals (device storage owned by the caller)
+    struct Functional {
+        int64_t* idx;
+        double* w;
+        double* acc;        // [0] block value being formed, [1] Welford mean, [2] M2
+        int64_t nterms;
+        std::vector<int64_t> pairs;
+        std::vector<double> weights;
+    };
+    std::vector<Functional> funcs;
     int64_t t = 0, nsamp = 0, accumulated = 0, inblock = 0, nfill = 0, nblocks = 0, launches = 0;
     int primed = 0, cur = 0;
     std::string last_error;
@@ -516,6 +526,17 @@ fth_status flush(fth_ctx* c) {
     const Layout& L = c->L;
     const double inv = 1.0 / ((double)c->block * (double)L.R);
     const double nb = (double)(c->nblocks + 1);
+    // functionals first: they read the block's partial sums before the flush clears them
+    for (auto& f : c->funcs) {
+        const bool p64 = L.path == kPathDense64;
+        cudaStream_t st = p64 ? c->stream : c->side;
+        FTH_CK(launch_functional_block(p64 ? nullptr : static_cast<const float*>(c->partial),
+                                       p64 ? static_cast<const double*>(c->partial) : nullptr,
+                                       L.R, L.count, f.idx, f.w, f.nterms, inv, nb, f.acc, c->err,
+                                       st),
+               "functional");
+        c->launches += 2;
+    }
     if (L.path == kPathDense64) {
         ProfScope ps(c, FTH_K_FLUSH);
         FTH_CK(launch_flush64(static_cast<double*>(c->partial), L.R, L.count, c->mean, c->m2,
@@ -1045,6 +1066,93 @@ fth_status fth_status_poll(fth_ctx* c) {
     return FTH_OK;
 }
 
+// Accumulator index of element (i, j), or a NOT_TRACKED / INVALID_ARG status.
+static fth_status element_index(fth_ctx* c, int64_t i, int64_t j, int64_t* out) {
+    const Layout& L = c->L;
+    if (i < 0 || j < 0 || i >= L.N || j >= L.N) {
+        c->last_error = "pair index out of range";
+        return FTH_E_INVALID_ARG;
+    }
+    if (L.track == FTH_TRACK_ALL && L.path == kPathDense32) {
+        *out = packed_index(i, j, L.nbt);
+        return FTH_OK;
+    }
+    auto it = c->pair_index.find(pair_key(i, j));
+    if (it == c->pair_index.end()) {
+        c->last_error = "element (" + std::to_string(i) + ", " + std::to_string(j) + ") is not tracked";
+        return FTH_E_NOT_TRACKED;
+    }
+    *out = it->second;
+    return FTH_OK;
+}
+
+size_t fth_functional_bytes(int64_t nterms) {
+    return nterms < 0 ? 0 : align256((size_t)nterms * 16 + 64);
+}
+
+fth_status fth_functional_add(fth_ctx* c, const int64_t* pairs, const double* weights,
+                              int64_t nterms, void* device_buffer, size_t bytes, int64_t* id) {
+    if (!c || !id || nterms < 0 || (nterms > 0 && (!pairs || !weights)) || !device_buffer)
+        return fail(c ? &c->last_error : nullptr, FTH_E_INVALID_ARG, "bad functional arguments");
+    if (bytes < fth_functional_bytes(nterms) || (reinterpret_cast<uintptr_t>(device_buffer) & 255u)) {
+        c->last_error = "functional buffer too small or not 256-byte aligned";
+        return FTH_E_WORKSPACE;
+    }
+    if (c->nblocks > 0 || c->inblock > 0) {
+        c->last_error = "functionals must be added before the first sample is accumulated";
+        return FTH_E_INVALID_ARG;
+    }
+    std::vector<int64_t> idx((size_t)nterms);
+    for (int64_t k = 0; k < nterms; ++k) {
+        const fth_status st = element_index(c, pairs[2 * k], pairs[2 * k + 1], &idx[k]);
+        if (st != FTH_OK) return st;
+        if (!std::isfinite(weights[k])) {
+            c->last_error = "non-finite functional weight";
+            return FTH_E_INVALID_ARG;
+        }
+    }
+    fth_ctx::Functional f;
+    uint8_t* b = static_cast<uint8_t*>(device_buffer);
+    f.acc = reinterpret_cast<double*>(b);
+    f.idx = reinterpret_cast<int64_t*>(b + 64);
+    f.w = reinterpret_cast<double*>(b + 64 + (size_t)nterms * 8);
+    f.nterms = nterms;
+    f.pairs.assign(pairs, pairs + 2 * nterms);
+    f.weights.assign(weights, weights + nterms);
+    FTH_CK(cudaMemsetAsync(f.acc, 0, 64, c->stream), "zero functional");
+    if (nterms) {
+        FTH_CK(cudaMemcpyAsync(f.idx, idx.data(), nterms * 8, cudaMemcpyHostToDevice, c->stream),
+               "h2d functional idx");
+        FTH_CK(cudaMemcpyAsync(f.w, weights, nterms * 8, cudaMemcpyHostToDevice, c->stream),
+               "h2d functional weights");
+    }
+    FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+    c->funcs.push_back(std::move(f));
+    *id = (int64_t)c->funcs.size() - 1;
+    return FTH_OK;
+}
+
+fth_status fth_functional(fth_ctx* c, int64_t id, double* value, double* errbar) {
+    if (!c || !value || id < 0 || id >= (int64_t)c->funcs.size())
+        return fail(c ? &c->last_error : nullptr, FTH_E_INVALID_ARG, "bad functional id");
+    const auto& f = c->funcs[id];
+    std::vector<double> v((size_t)f.nterms);
+    fth_status st = fth_elements(c, f.pairs.data(), f.nterms, v.data(), nullptr);
+    if (st != FTH_OK) return st;
+    double sum = 0.0;
+    for (int64_t k = 0; k < f.nterms; ++k) sum += f.weights[k] * v[k];
+    *value = f.nterms ? sum : 0.0;
+    if (errbar) {
+        double acc[3];
+        FTH_CK(cudaMemcpyAsync(acc, f.acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream),
+               "d2h functional");
+        FTH_CK(cudaStreamSynchronize(c->stream), "sync");
+        const double nb = (double)c->nblocks;
+        *errbar = nb >= 2 ? std::sqrt(acc[2] / (nb * (nb - 1.0))) : NAN;
+    }
+    return FTH_OK;
+}
+
 fth_status fth_elements(fth_ctx* c, const int64_t* pairs, int64_t k, double* values,
                         double* errbars) {
     if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
@@ -1057,22 +1165,8 @@ fth_status fth_elements(fth_ctx* c, const int64_t* pairs, int64_t k, double* val
     const Layout& L = c->L;
     std::vector<int64_t> idx((size_t)k);
     for (int64_t e = 0; e < k; ++e) {
-        const int64_t i = pairs[2 * e], j = pairs[2 * e + 1];
-        if (i < 0 || j < 0 || i >= L.N || j >= L.N) {
-            c->last_error = "pair index out of range";
-            return FTH_E_INVALID_ARG;
-        }
-        if (L.track == FTH_TRACK_ALL && L.path == kPathDense32) {
-            idx[e] = packed_index(i, j, L.nbt);
-        } else {
-            auto it = c->pair_index.find(pair_key(i, j));
-            if (it == c->pair_index.end()) {
-                c->last_error = "element (" + std::to_string(i) + ", " + std::to_string(j) +
-                                ") is not tracked";
-                return FTH_E_NOT_TRACKED;
-            }
-            idx[e] = it->second;
-        }
+        st = element_index(c, pairs[2 * e], pairs[2 * e + 1], &idx[e]);
+        if (st != FTH_OK) return st;
     }
     const double nb = (double)c->nblocks;
     const double nacc = (double)(c->nblocks * c->block + c->inblock);

@@ -95,6 +95,12 @@ __host__ __device__ inline int64_t packed_index(int64_t i, int64_t j, int64_t nb
     return tile * (int64_t)kTile * kTile + (i % kTile) * kTile + (j % kTile);
 }
 
+// Linear functional of tracked elements: fold one completed block (see the kernel).
+cudaError_t launch_functional_block(const float* partial32, const double* partial64, int64_t R,
+                                    int64_t stride, const int64_t* idx, const double* w,
+                                    int64_t nterms, double inv_count, double nb, double* acc,
+                                    uint32_t* err, cudaStream_t st);
+
 // Conversions used at create / set_state.
 cudaError_t launch_round_tf32(float* x, int64_t n, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);

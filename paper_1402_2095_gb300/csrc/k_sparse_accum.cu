@@ -249,6 +249,65 @@ cudaError_t launch_flush64(double* partial, int64_t R, int64_t stride, double* m
     return cudaGetLastError();
 }
 
+// -------------------------------------------------------------- linear functionals
+// A functional L = sum_k w_k <x_{i_k} x_{j_k}> of tracked elements (e.g. Tr f(M) with
+// unit weights on the diagonal, Tr O f(M) with the entries of a symmetric O, Eq. 6 and
+// the trace forms of Sec. "The f-thermostat").  At each block flush, before the
+// element partials are cleared, the block value sum_k w_k (block mean of element
+// idx_k) is formed (acc[0], by atomics) and folded into FP64 Welford sums (acc[1],
+// acc[2]) so the functional gets its own block error bar.
+__global__ void functional_block_kernel(const float* __restrict__ partial32,
+                                        const double* __restrict__ partial64, int64_t R,
+                                        int64_t stride, const int64_t* __restrict__ idx,
+                                        const double* __restrict__ w, int64_t nterms,
+                                        double inv_count, double* __restrict__ acc) {
+    double sum = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nterms;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = idx[k];
+        double part = 0.0;
+        if (partial32) part = (double)partial32[e];
+        if (partial64)
+            for (int64_t r = 0; r < R; ++r) part += partial64[r * stride + e];
+        sum += w[k] * part * inv_count;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        atomicAdd(acc, t);
+    }
+}
+
+__global__ void functional_fold_kernel(double* __restrict__ acc, double nb, uint32_t* err) {
+    const double b = acc[0];
+    if (!isfinite(b)) atomicOr(err, kErrNonFinite);
+    const double d = b - acc[1];
+    const double mu = acc[1] + d / nb;
+    acc[2] += d * (b - mu);
+    acc[1] = mu;
+    acc[0] = 0.0;
+}
+
+cudaError_t launch_functional_block(const float* partial32, const double* partial64, int64_t R,
+                                    int64_t stride, const int64_t* idx, const double* w,
+                                    int64_t nterms, double inv_count, double nb, double* acc,
+                                    uint32_t* err, cudaStream_t st) {
+    if (nterms > 0) {
+        const unsigned blocks = (unsigned)std::min<int64_t>((nterms + 255) / 256, 152 * 4);
+        functional_block_kernel<<<blocks, 256, 0, st>>>(partial32, partial64, R, stride, idx, w,
+                                                        nterms, inv_count, acc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    functional_fold_kernel<<<1, 1, 0, st>>>(acc, nb, err);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- gather for fth_elements
 __global__ void gather_kernel(const int64_t* __restrict__ idx, int64_t k,
                               const double* __restrict__ mean, const double* __restrict__ m2,

@@ -319,3 +319,59 @@ def test_full_size_lattice_sampled():
         assert abs(q1[r, i] - qn[k]) <= 1e-5 * (1 + abs(qn[k]))
         assert abs(p1[r, i] - pn[k]) <= 1e-5 * (1 + abs(pn[k]))
         assert np.allclose(s1[r, :, i], sn[k], rtol=1e-5, atol=1e-5)
+
+
+# ------------------------------------------------------------------ linear functionals
+def _functional_from_samples(samples, burnin, block, pairs, w):
+    """Value and block error bar of sum_k w_k <x_i x_j> straight from the oracle's
+    samples (steps, R, n): per-sample replica averages, blocks of `block` samples."""
+    x = samples[burnin:]
+    per = np.einsum("k,tkr->t", w, x[:, :, pairs[:, 0]].transpose(0, 2, 1) *
+                    x[:, :, pairs[:, 1]].transpose(0, 2, 1)) / x.shape[1]
+    nb = per.shape[0] // block
+    bm = per[:nb * block].reshape(nb, block).mean(axis=1)
+    err = np.sqrt(np.sum((bm - bm.mean()) ** 2) / (nb * (nb - 1))) if nb >= 2 else np.nan
+    return per.mean(), err
+
+
+def test_functionals_csr_trace_and_trace_with_operator():
+    """Tr f(M) and Tr M f(M) on a lattice (tracked: diagonal + nearest neighbours)."""
+    import scipy.sparse as sp
+    from paper_1402_2095_gb300.binding import trace_terms
+    L = 5
+    n = L ** 3
+    rowptr, col, val = syn.lattice_csr(L, seed=31)
+    a, c = syn.random_gle(4, seed=32, rate=2.0)
+    pairs = np.concatenate([syn.diag_pairs(n), syn.lattice_nn_pairs(L)])
+    g, o = make_pair(csr=(rowptr, col, val, n), a_p=a, c_p=c, dt=0.1 / np.sqrt(14.5), R=8,
+                     seed=33, pairs=pairs, burnin=20, block=40)
+    Mo = sp.csr_matrix((val.astype(np.float32).astype(np.float64), col, rowptr), shape=(n, n))
+    terms = [trace_terms(n=n), trace_terms(O=Mo)]
+    ids = [g.add_functional(p, w) for p, w in terms]
+    g.run(420)
+    samples = o.run(420, keep_samples=True)
+    for fid, (p, w) in zip(ids, terms):
+        v, e = g.functional(fid)
+        vo, eo = _functional_from_samples(samples, 20, 40, p, w)
+        assert abs(v - vo) <= 1e-4 * abs(vo)
+        assert abs(e - eo) <= 1e-3 * eo
+        # the value is the weighted sum of the element estimates
+        ve, _ = g.elements(p)
+        assert abs(v - float(np.dot(w, ve))) <= 1e-12 * abs(v)
+
+
+def test_functional_fp64_dense_operator():
+    from paper_1402_2095_gb300.binding import trace_terms
+    n = 12
+    M = _dense(n)
+    a, c = syn.random_gle(3, seed=34, rate=3.0)
+    g, o = make_pair(M, a_p=a, c_p=c, dt=0.01, R=4, seed=35, precision="fp64", track="all",
+                     burnin=0, block=25)
+    p, w = trace_terms(O=M)
+    fid = g.add_functional(p, w)
+    g.run(250)
+    samples = o.run(250, keep_samples=True)
+    v, e = g.functional(fid)
+    vo, eo = _functional_from_samples(samples, 0, 25, p, w)
+    assert abs(v - vo) <= 1e-10 * abs(vo)
+    assert abs(e - eo) <= 1e-8 * eo

@@ -24,7 +24,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(ROOT, "include", "fth.h")).read()
-    declared = set(re.findall(r"^\s*(?:fth_status|const char\s*\*|void|double|fth_pool\s*\*)\s+(fth_\w+)\s*\(", hdr,
+    declared = set(re.findall(r"^\s*(?:fth_status|const char\s*\*|void|double|size_t|fth_pool\s*\*)\s+(fth_\w+)\s*\(", hdr,
                               flags=re.M))
     assert declared == set(B.EXPORTS)
     for name in declared:
@@ -98,3 +98,23 @@ def test_binary_is_sm103a_only(lib):
     # the build compiles for sm_103a and nothing else
     from paper_1402_2095_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_trace_terms_weights():
+    """sum_k w_k F_{i_k j_k} = Tr(O F) for symmetric O and F (dense and sparse O), and
+    the unit-weight form gives Tr F."""
+    import scipy.sparse as sp
+    from paper_1402_2095_gb300.binding import trace_terms
+    g = np.random.default_rng(5)
+    n = 9
+    A = g.standard_normal((n, n))
+    O = A + A.T
+    O[np.abs(O) < 0.5] = 0.0
+    B = g.standard_normal((n, n))
+    F = B + B.T
+    for op in (O, sp.csr_matrix(O)):
+        p, w = trace_terms(O=op)
+        assert np.isclose(np.sum(w * F[p[:, 0], p[:, 1]]), np.trace(O @ F))
+        assert np.all(p[:, 0] <= p[:, 1])
+    p, w = trace_terms(n=n)
+    assert np.isclose(np.sum(w * F[p[:, 0], p[:, 1]]), np.trace(F))
