@@ -40,6 +40,8 @@ class OracleFTH:
             T, S = gle.propagator(a_p, c_p, dt)
         self.T = np.ascontiguousarray(T, dtype=np.float64)
         self.S = np.ascontiguousarray(S, dtype=np.float64)
+        self.T2 = np.ascontiguousarray(self.T @ self.T)
+        self.Lj = np.ascontiguousarray(gle.joint_noise(self.T, self.S))
         self.ns = self.T.shape[0]
         self.dt = float(dt)
         self.R = int(replicas)
@@ -69,11 +71,12 @@ class OracleFTH:
         self.p[...] = p
         self.s[...] = s
 
-    def _common(self):
+    def _common(self, joint=False):
         P = native.ptr
-        return (native.I64(self.n), native.I64(self.R), native.INT(self.ns), native.INT(self.kind),
-                P(self.Md), P(self.rowptr), P(self.col), P(self.val), P(self.T), P(self.S),
-                native.D(self.dt), native.U64(self.seed), native.U32(self.roff))
+        head = (native.I64(self.n), native.I64(self.R), native.INT(self.ns), native.INT(self.kind),
+                P(self.Md), P(self.rowptr), P(self.col), P(self.val), P(self.T), P(self.S))
+        extra = (P(self.T2), P(self.Lj)) if joint else ()
+        return head + extra + (native.D(self.dt), native.U64(self.seed), native.U32(self.roff))
 
     def run(self, steps: int, keep_samples: bool = False):
         L = native.lib()
@@ -85,7 +88,7 @@ class OracleFTH:
                 raise RuntimeError(f"oracle_prologue rc={rc}")
             self.primed = True
         samples = np.zeros((steps, self.R, self.n)) if keep_samples else None
-        rc = L.oracle_steps(*self._common(), native.U32(self.t + 1), native.I64(steps),
+        rc = L.oracle_steps(*self._common(joint=True), native.U32(self.t + 1), native.I64(steps),
                             P(self.q), P(self.p), P(self.s), native.INT(self.observable),
                             P(samples), native.I64(len(self.pairs)), P(self.pairs),
                             native.I64(self.burnin), native.I64(self.block),
@@ -131,12 +134,14 @@ def force(M, q):
 def fused_step_elements(M, q, p, s, T, S, dt, seed, kappa, elems, observable=0):
     """One fused launch (kick index kappa) for a few sampled (i, r), computed one by
     one: force (M q_r)_i from the full current positions, then B(dt/2), O(dt/2),
-    sample, O(dt/2), B(dt/2), A(dt) on that (i, r) alone.
+    sample, O(dt/2), B(dt/2), A(dt) on that (i, r) alone (the two O half-steps drawn
+    jointly, gle.joint_noise).
 
     M: [N][N] float64 array or scipy.sparse CSR matrix, q/p: [R][N], s: [R][ns-1][N];
     elems: iterable of (i, r).
     Returns arrays (q_new, p_new, s_new[ns-1], sample) per element."""
     ns = T.shape[0]
+    Lj = gle.joint_noise(T, S)
     out_q, out_p, out_s, out_x = [], [], [], []
     for i, r in elems:
         i, r = int(i), int(r)
@@ -144,13 +149,13 @@ def fused_step_elements(M, q, p, s, T, S, dt, seed, kappa, elems, observable=0):
             mq = float((M.getrow(i) @ q[r])[0])
         else:
             mq = float(np.dot(M[i], q[r]))
-        xi = native.normals(seed, kappa, i, r, 2 * ns)
+        zeta = native.normals(seed, kappa, i, r, ns + 1)
         v = np.concatenate([[p[r, i]], s[r, :, i]])
         qi = float(q[r, i])
         v[0] -= 0.5 * dt * mq
-        v = T @ v + S @ xi[:ns]
-        x = qi if observable else v[0]
-        v = T @ v + S @ xi[ns:]
+        xy = Lj @ zeta                     # joint noise of the two O half-steps
+        x = qi if observable else float(T[0] @ v + xy[0])
+        v = T @ (T @ v) + xy[1:]
         v[0] -= 0.5 * dt * mq
         qi += dt * v[0]
         out_q.append(qi)

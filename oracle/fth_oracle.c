@@ -22,9 +22,17 @@
  * (seed_lo, seed_hi).  Each uint32 pair (x0,x1) gives two normals:
  *   u(x) = ((x >> 9) * 2 + 1) * 2^-24,  rho = sqrt(-2 ln u(x0)),
  *   n0 = rho cos(2 pi u(x1)),  n1 = rho sin(2 pi u(x1)).
- * Normals 0..ns-1 of kappa drive the O half-step that ends step kappa-1,
- * normals ns..2ns-1 drive the O half-step that starts step kappa.  The replica
- * index in the counter is r + roff (roff: global index of the first replica).
+ * The replica index in the counter is r + roff (roff: global index of the first
+ * replica).
+ *
+ * The two O half-steps of a fused launch (ending step kappa-1 and starting step
+ * kappa) are separated only by the end-of-step sample, which observes p after the
+ * first one.  They are drawn jointly from their exact joint law: with v the state
+ * after the end-of-step kick, the sample is (T v)_0 + x and the next state is
+ * T^2 v + y, where (x, y) = L zeta, zeta = normals 0..ns of kappa, and L L^T is the
+ * covariance of (x, y) = (e_0^T S xi1, T S xi1 + S xi2) -- the same Markov chain as
+ * two independent half-steps, with ns + 1 normals instead of 2 ns.  The prologue
+ * (start half only) uses normals 0..ns-1 of its kappa for a single O half-step.
  *
  * State layout: q[R][n], p[R][n], s[R][ns-1][n]  (replica-major).
  */
@@ -149,9 +157,9 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
     for (int64_t r = 0; r < R; ++r) {
         double xi[2 * NS_MAX], v[NS_MAX];
         for (int64_t i = 0; i < n; ++i) {
-            oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, 2 * ns, xi);
+            oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, ns, xi);
             load_v(n, ns, r, i, p, s, v);
-            o_half(ns, T, S, v, xi + ns);
+            o_half(ns, T, S, v, xi);
             v[0] += 0.5 * dt * F[r * n + i];
             store_v(n, ns, r, i, p, s, v);
             q[r * n + i] += dt * v[0];
@@ -165,7 +173,8 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
  * `nsteps` fused step pairs.  Launch j (kick index kappa0 + j) computes the force at
  * the current positions, finishes the current step (B, O, sample) and starts the
  * next one (O, B, A).  Samples are written to `samples` ([nsteps][R][n]) when it is
- * non-NULL.
+ * non-NULL.  T2 = T T ([ns][ns]) and Lj ([ns+1][ns+1], lower) give the joint O
+ * half-steps described at the top of this file.
  *
  * Accumulation over the tracked pairs (i, j) of x = p (observable 0) or q (1):
  *   nsamp      samples seen so far (burn-in included); samples with index < burnin
@@ -177,7 +186,8 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
  */
 int oracle_steps(int64_t n, int64_t R, int ns, int kind, const double* Md,
                  const int64_t* rowptr, const int64_t* col, const double* val,
-                 const double* T, const double* S, double dt, uint64_t seed,
+                 const double* T, const double* S, const double* T2, const double* Lj,
+                 double dt, uint64_t seed,
                  uint32_t roff, uint32_t kappa0, int64_t nsteps, double* q, double* p, double* s,
                  int observable, double* samples,
                  int64_t npairs, const int64_t* pairs, int64_t burnin, int64_t block,
@@ -197,15 +207,25 @@ int oracle_steps(int64_t n, int64_t R, int ns, int kind, const double* Md,
         force(n, R, kind, Md, rowptr, col, val, q, F);
 #pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < R; ++r) {
-            double xi[2 * NS_MAX], v[NS_MAX];
+            double zeta[NS_MAX + 4], v[NS_MAX], out[NS_MAX];
+            const int m = ns + 1;
             for (int64_t i = 0; i < n; ++i) {
                 const double f = F[r * n + i];
-                oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, 2 * ns, xi);
+                oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, m, zeta);
                 load_v(n, ns, r, i, p, s, v);
                 v[0] += 0.5 * dt * f;          /* B(dt/2), end of the current step */
-                o_half(ns, T, S, v, xi);       /* O(dt/2), end of the current step */
-                X[r * n + i] = observable ? q[r * n + i] : v[0];
-                o_half(ns, T, S, v, xi + ns);  /* O(dt/2), start of the next step */
+                /* p after the end-of-step O(dt/2): (T v)_0 + x, x = (L zeta)_0 */
+                double pmid = Lj[0] * zeta[0];
+                for (int b = 0; b < ns; ++b) pmid += T[b] * v[b];
+                X[r * n + i] = observable ? q[r * n + i] : pmid;
+                /* both O(dt/2): T^2 v + y, y = (L zeta)_1..ns */
+                for (int a = 0; a < ns; ++a) {
+                    double acc = 0.0;
+                    for (int b = 0; b < ns; ++b) acc += T2[a * ns + b] * v[b];
+                    for (int b = 0; b <= a + 1; ++b) acc += Lj[(a + 1) * m + b] * zeta[b];
+                    out[a] = acc;
+                }
+                for (int a = 0; a < ns; ++a) v[a] = out[a];
                 v[0] += 0.5 * dt * f;          /* B(dt/2) */
                 store_v(n, ns, r, i, p, s, v);
                 q[r * n + i] += dt * v[0];     /* A(dt) */

@@ -49,6 +49,26 @@ def chol_psd(sig: np.ndarray, rel: float = 1e-14) -> np.ndarray:
     return L
 
 
+def joint_noise(T: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """Factor L ((ns+1) x (ns+1), lower) of the joint law of the two O half-steps
+    around the end-of-step sample (Eq. 2's exact Ornstein-Uhlenbeck half-step, applied
+    twice with the sample of p in between).  From a state v the sample is
+    (T v)_0 + x and the next state T T v + y with x = e_0^T S xi1, y = T S xi1 + S xi2;
+    (x, y) is Gaussian with covariance
+        [[C1_00,      (T C1 e_0)^T     ],
+         [T C1 e_0,   T C1 T^T + C1    ]],  C1 = S S^T,
+    factored by chol_psd (same zero-pivot rule as S)."""
+    T = np.asarray(T, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    ns = T.shape[0]
+    C1 = S @ S.T
+    sig = np.zeros((ns + 1, ns + 1))
+    sig[0, 0] = C1[0, 0]
+    sig[1:, 0] = sig[0, 1:] = T @ C1[:, 0]
+    sig[1:, 1:] = T @ C1 @ T.T + C1
+    return chol_psd(sig)
+
+
 def propagator(a_p: np.ndarray, c_p: np.ndarray, dt: float):
     """(T, S) of the O half-step: T = exp(-A_p dt/2), S = chol(C_p - T C_p T^T)."""
     a_p = np.asarray(a_p, dtype=np.float64)

@@ -52,8 +52,8 @@ def _declare(L):
     L.oracle_normals.restype = None
     L.oracle_prologue.argtypes = [I64, I64, INT, INT, P, P, P, P, P, P, D, U64, U32, U32, P, P, P]
     L.oracle_prologue.restype = INT
-    L.oracle_steps.argtypes = ([I64, I64, INT, INT, P, P, P, P, P, P, D, U64, U32, U32, I64, P, P, P,
-                                INT, P, I64, P, I64, I64, P, P, P, P, P, P])
+    L.oracle_steps.argtypes = ([I64, I64, INT, INT, P, P, P, P, P, P, P, P, D, U64, U32, U32, I64, P,
+                                P, P, INT, P, I64, P, I64, I64, P, P, P, P, P, P])
     L.oracle_steps.restype = INT
     L.oracle_force.argtypes = [I64, I64, INT, P, P, P, P, P, P]
     L.oracle_force.restype = None

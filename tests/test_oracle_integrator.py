@@ -71,11 +71,23 @@ def _python_integrator(Mfull, T, S, dt, seed, R, steps):
         return np.array([sum(T[a, b] * vec[b] for b in range(ns))
                          + sum(S[a, b] * xi[b] for b in range(a + 1)) for a in range(ns)])
 
+    # joint law of (sample noise, two-half-step noise), written out from its definition
+    C1 = S @ S.T
+    sig = np.zeros((ns + 1, ns + 1))
+    sig[0, 0] = C1[0, 0]
+    for a in range(ns):
+        sig[a + 1, 0] = sig[0, a + 1] = sum(T[a, b] * C1[b, 0] for b in range(ns))
+    TCT = T @ C1 @ T.T
+    for a in range(ns):
+        for b in range(ns):
+            sig[a + 1, b + 1] = TCT[a, b] + C1[a, b]
+    Lj = gle.chol_psd(sig)
+
     f = F(q)
     for r in range(R):
         for i in range(n):
-            xi = native.normals(seed, 0, i, r, 2 * ns)
-            v[r, i] = O(v[r, i], xi[ns:])
+            xi = native.normals(seed, 0, i, r, ns)
+            v[r, i] = O(v[r, i], xi)
             v[r, i, 0] += 0.5 * dt * f[r, i]
             q[r, i] += dt * v[r, i, 0]
     samples = []
@@ -84,11 +96,12 @@ def _python_integrator(Mfull, T, S, dt, seed, R, steps):
         X = np.zeros((R, n))
         for r in range(R):
             for i in range(n):
-                xi = native.normals(seed, t, i, r, 2 * ns)
+                zeta = native.normals(seed, t, i, r, ns + 1)
+                xy = [sum(Lj[a, b] * zeta[b] for b in range(a + 1)) for a in range(ns + 1)]
                 v[r, i, 0] += 0.5 * dt * f[r, i]
-                v[r, i] = O(v[r, i], xi[:ns])
-                X[r, i] = v[r, i, 0]
-                v[r, i] = O(v[r, i], xi[ns:])
+                X[r, i] = sum(T[0, b] * v[r, i, b] for b in range(ns)) + xy[0]
+                tv = [sum(T[a, b] * v[r, i, b] for b in range(ns)) for a in range(ns)]
+                v[r, i] = [sum(T[a, b] * tv[b] for b in range(ns)) + xy[a + 1] for a in range(ns)]
                 v[r, i, 0] += 0.5 * dt * f[r, i]
                 q[r, i] += dt * v[r, i, 0]
         samples.append(X)
@@ -187,3 +200,29 @@ def test_elementwise_step_equals_c_integrator():
         assert np.isclose(pn[k], o.p[r, i], rtol=1e-13, atol=1e-14)
         assert np.allclose(sn[k], o.s[r, :, i], rtol=1e-13, atol=1e-14)
         assert np.isclose(xn[k], x[r, i], rtol=1e-13, atol=1e-14)
+
+
+def test_joint_half_steps_have_the_two_step_law():
+    """The joint draw reproduces the law of two independent O half-steps around the
+    sample: L L^T equals the covariance of (e_0^T S xi1, T S xi1 + S xi2) formed by
+    brute force over a basis of (xi1, xi2), and for s = 0 it reduces to the scalar
+    closed form."""
+    a, c = syn.random_gle(4, seed=41, rate=2.5)
+    T, S = gle.propagator(a, c, 0.07)
+    ns = T.shape[0]
+    Lj = gle.joint_noise(T, S)
+    assert np.allclose(np.triu(Lj, 1), 0.0)
+    # the map (xi1, xi2) -> (x, y) is linear: its matrix K gives the covariance K K^T
+    K = np.zeros((ns + 1, 2 * ns))
+    for k in range(2 * ns):
+        e = np.zeros(2 * ns)
+        e[k] = 1.0
+        x = (S @ e[:ns])[0]
+        y = T @ (S @ e[:ns]) + S @ e[ns:]
+        K[:, k] = np.concatenate([[x], y])
+    assert np.allclose(Lj @ Lj.T, K @ K.T, rtol=1e-12, atol=1e-14)
+    # s = 0: T = t, S = sqrt(1 - t^2) (unit kT): x ~ N(0, 1 - t^2), y = t x' + ...
+    t = 0.8
+    L0 = gle.joint_noise(np.array([[t]]), np.array([[np.sqrt(1 - t * t)]]))
+    c1 = 1 - t * t
+    assert np.allclose(L0 @ L0.T, [[c1, t * c1], [t * c1, t * t * c1 + c1]])
