@@ -132,6 +132,56 @@ void chol_psd(int n, const double* a_in, double* L) {
     }
 }
 
+}  // namespace
+
+// The sample (end of step kappa - 1) observes p between the two O half-steps of a fused
+// launch.  From the state v after the end-of-step kick, the sample is (T v)_0 + x and
+// the next mid-step state T T v + y, with x = e_0^T S xi1 and y = T S xi1 + S xi2 for
+// independent xi1, xi2.  (x, y) is Gaussian with covariance
+//   [[C1_00, (T C1 e_0)^T], [T C1 e_0, T C1 T^T + C1]],  C1 = S S^T,
+// so L = chol of it draws both half-steps from ns + 1 normals: the same Markov chain.
+void fth::fill_gle_constants(int ns, const double* T, const double* S, GleF32* g32, GleF64* g64) {
+    const int m = ns + 1;
+    std::vector<double> C1(ns * ns, 0.0), TC1(ns * ns, 0.0), sig(m * m, 0.0), L(m * m, 0.0);
+    for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j)
+            for (int k = 0; k < ns; ++k) C1[i * ns + j] += S[i * ns + k] * S[j * ns + k];
+    mat_mul(ns, T, C1.data(), TC1.data());
+    sig[0] = C1[0];
+    for (int a = 0; a < ns; ++a) sig[(a + 1) * m] = sig[a + 1] = TC1[a * ns];
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            double tct = 0.0;
+            for (int k = 0; k < ns; ++k) tct += TC1[a * ns + k] * T[b * ns + k];
+            sig[(a + 1) * m + b + 1] = tct + C1[a * ns + b];
+        }
+    chol_psd(m, sig.data(), L.data());
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+            const double d = T[a * ns + b] - (a == b ? 1.0 : 0.0);
+            double t2 = 0.0;
+            for (int k = 0; k < ns; ++k) t2 += T[a * ns + k] * T[k * ns + b];
+            const double d2 = t2 - (a == b ? 1.0 : 0.0);
+            if (g32) {
+                g32->T[a * kMaxNs + b] = (float)d;
+                g32->S[a * kMaxNs + b] = (float)S[a * ns + b];
+                g32->D2[a * kMaxNs + b] = (float)d2;
+            }
+            if (g64) {
+                g64->T[a * kMaxNs + b] = d;
+                g64->S[a * kMaxNs + b] = S[a * ns + b];
+                g64->D2[a * kMaxNs + b] = d2;
+            }
+        }
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            if (g32) g32->L[a * kMaxNs1 + b] = (float)L[a * m + b];
+            if (g64) g64->L[a * kMaxNs1 + b] = L[a * m + b];
+        }
+}
+
+namespace {
+
 fth_status propagator(const fth_gle* gle, double dt, double* T, double* S, std::string* msg) {
     if (!gle) return fail(msg, FTH_E_INVALID_ARG, "gle is NULL");
     const int ns = gle->s + 1;
@@ -279,7 +329,7 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_p = c.take((size_t)L->R * Np * 8);
         L->off_s = c.take((size_t)std::max(nsub, 1) * L->R * Np * 8);
         // normals generated ahead: up to 4096 kick indices, at most ~64 MiB
-        const size_t per = (size_t)L->R * 2 * L->ns * Np * 8;
+        const size_t per = (size_t)L->R * (L->ns + 1) * Np * 8;
         L->xi_chunk = std::max<int64_t>(2, std::min<int64_t>(4096, (int64_t)((size_t(64) << 20) / per)));
         L->off_xi = c.take(per * (size_t)L->xi_chunk);
     }
@@ -812,15 +862,7 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
         delete c;
         return st;
     }
-    const int ns = L.ns;
-    for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b) {
-            const double d = c->T[a * ns + b] - (a == b ? 1.0 : 0.0);   // D = T - I
-            c->g32.T[a * kMaxNs + b] = (float)d;
-            c->g32.S[a * kMaxNs + b] = (float)c->S[a * ns + b];
-            c->g64.T[a * kMaxNs + b] = d;
-            c->g64.S[a * kMaxNs + b] = c->S[a * ns + b];
-        }
+    fill_gle_constants(L.ns, c->T, c->S, &c->g32, &c->g64);
     c->g32.dt = (float)opt->dt;
     c->g32.hdt = (float)(0.5 * opt->dt);
     c->g64.dt = opt->dt;

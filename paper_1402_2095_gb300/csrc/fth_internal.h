@@ -13,9 +13,17 @@ constexpr int kTile = 128;         // tcgen05 M tile (rows per CTA) and SYRK til
 
 // O half-step constants in FP32 (the FP64 originals are built on the host).
 // T holds D = T - I (the increment form used by the O half-step), S is lower triangular.
+// O half-step constants.  T holds D = T - I (the increment form keeps FP32 rounding
+// small), S the noise factor of one half-step.  A fused launch applies the two
+// half-steps around the end-of-step sample jointly: D2 = T T - I, and L
+// ([ns+1][ns+1], lower, row stride kMaxNs + 1) factors the joint covariance of the
+// sample's noise and the two half-steps' noise (ns + 1 normals).
+constexpr int kMaxNs1 = kMaxNs + 1;
 struct GleF32 {
     float T[kMaxNs * kMaxNs];
     float S[kMaxNs * kMaxNs];
+    float D2[kMaxNs * kMaxNs];
+    float L[kMaxNs1 * kMaxNs1];
     float dt, hdt;
     uint32_t key0, key1;
     uint32_t roff;   // replica offset in the noise counter
@@ -33,10 +41,17 @@ inline void set_round_keys(GleF32& g) {
 struct GleF64 {
     double T[kMaxNs * kMaxNs];
     double S[kMaxNs * kMaxNs];
+    double D2[kMaxNs * kMaxNs];
+    double L[kMaxNs1 * kMaxNs1];
     double dt, hdt;
     uint32_t key0, key1;
     uint32_t roff;
 };
+
+// Fills the O half-step constants of both precisions (either may be NULL) from the
+// FP64 propagator T, S ([ns][ns], row-major): D = T - I, S, D2 = T T - I and the
+// joint factor L of the two half-steps around the end-of-step sample.
+void fill_gle_constants(int ns, const double* T, const double* S, GleF32* g32, GleF64* g64);
 
 // Bits of the device error word.
 enum : uint32_t { kErrTimeout = 1u, kErrNonFinite = 2u };

@@ -6,8 +6,9 @@
 // counter (kappa, i, r, k) and key (seed_lo, seed_hi).  Box-Muller turns each uint32
 // pair (a, b) into two normals rho*cos(2 pi u_b), rho*sin(2 pi u_b) with
 // rho = sqrt(-2 ln u_a) and u(x) = ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and
-// never 0 or 1.  Normals 0..ns-1 drive the O half-step ending step kappa-1, normals
-// ns..2ns-1 the O half-step starting step kappa.
+// never 0 or 1.  A fused launch (end of step kappa-1 and start of step kappa) uses
+// normals 0..ns of kappa for its two O half-steps, drawn jointly (gle_fused); a launch
+// with one half-step (the prologue) uses normals 0..ns-1.
 #pragma once
 
 #include <stdint.h>
@@ -62,20 +63,21 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
     z1 = -rho * sn;
 }
 
-// The 2*NS normals of (kappa, i, r).
+// The NS + 1 normals of (kappa, i, r) a fused launch needs.
 template <int NS>
 __device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t r,
-                                            const uint32_t* rk, float (&xi)[2 * NS]) {
-    constexpr int kCalls = (2 * NS + 3) / 4;
+                                            const uint32_t* rk, float (&xi)[NS + 1]) {
+    constexpr int kCount = NS + 1;
+    constexpr int kCalls = (kCount + 3) / 4;
 #pragma unroll
     for (int k = 0; k < kCalls; ++k) {
         const uint4 x = philox4x32_10_rk(make_uint4(kappa, i, r, (uint32_t)k), rk);
         float z[4];
         box_muller(x.x, x.y, z[0], z[1]);
-        box_muller(x.z, x.w, z[2], z[3]);
+        if (4 * k + 2 < kCount) box_muller(x.z, x.w, z[2], z[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (4 * k + j < 2 * NS) xi[4 * k + j] = z[j];
+            if (4 * k + j < kCount) xi[4 * k + j] = z[j];
     }
 }
 
@@ -99,20 +101,55 @@ __device__ __forceinline__ void o_half(Real (&v)[NS], const Real* D, const Real*
     for (int a = 0; a < NS; ++a) v[a] = out[a];
 }
 
+// The two O half-steps around the end-of-step sample, drawn jointly: with v the state
+// after the end-of-step kick, the sample (observable p) is (T v)_0 + (L zeta)_0 and the
+// next state T T v + (L zeta)_1..NS, zeta = NS + 1 normals.  Increment form as o_half.
+template <int NS, typename Real, typename G>
+__device__ __forceinline__ void o_joint(Real (&v)[NS], const G& g, const Real* zeta,
+                                        Real& pmid) {
+    Real inc = g.L[0] * zeta[0];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) inc = fma(g.T[b], v[b], inc);
+    pmid = v[0] + inc;
+    Real out[NS];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) acc = fma(g.D2[a * kMaxNs + b], v[b], acc);
+#pragma unroll
+        for (int b = 0; b <= a + 1; ++b) acc = fma(g.L[(a + 1) * kMaxNs1 + b], zeta[b], acc);
+        out[a] = v[a] + acc;
+    }
+#pragma unroll
+    for (int a = 0; a < NS; ++a) v[a] = out[a];
+}
+
 // One fused launch on one (i, r): mq = (M q)_i at the current positions.
-//   end   : p += -hdt mq;  O(xi[0..NS));  sample
-//   start : O(xi[NS..2NS));  p += -hdt mq;  q += dt p
+//   end + start : p += -hdt mq;  both O half-steps jointly, sample between;
+//                 p += -hdt mq;  q += dt p
+//   start only  : O(zeta[0..NS));  p += -hdt mq;  q += dt p       (prologue)
+//   end only    : p += -hdt mq;  O(zeta[0..NS));  sample
 template <int NS>
 __device__ __forceinline__ void gle_fused(float& q, float (&v)[NS], float mq, const GleF32& g,
-                                          const float (&xi)[2 * NS], int flags, int observable,
+                                          const float (&xi)[NS + 1], int flags, int observable,
                                           float& sample) {
+    if ((flags & kDoEnd) && (flags & kDoStart)) {
+        v[0] = fmaf(-g.hdt, mq, v[0]);
+        float pmid;
+        o_joint<NS, float>(v, g, xi, pmid);
+        sample = observable ? q : pmid;
+        v[0] = fmaf(-g.hdt, mq, v[0]);
+        q = fmaf(g.dt, v[0], q);
+        return;
+    }
     if (flags & kDoEnd) {
         v[0] = fmaf(-g.hdt, mq, v[0]);
         o_half<NS, float>(v, g.T, g.S, xi);
         sample = observable ? q : v[0];
     }
     if (flags & kDoStart) {
-        o_half<NS, float>(v, g.T, g.S, xi + NS);
+        o_half<NS, float>(v, g.T, g.S, xi);
         v[0] = fmaf(-g.hdt, mq, v[0]);
         q = fmaf(g.dt, v[0], q);
     }

@@ -27,8 +27,10 @@ __device__ __forceinline__ void box_muller64(uint32_t a, uint32_t b, double& z0,
     z1 = rho * sn;
 }
 
-// Noise ahead of the integrator: the 2 NS normals of every (kappa, i, r) of a segment of
-// `iters` kick indices from kappa0, written to xi[((it R + r) 2 NS + a) Np + i].  FP64
+// Noise ahead of the integrator: the NS + 1 normals of every (kappa, i, r) of a segment
+// of `iters` kick indices from kappa0, written to xi[((it R + r) (NS + 1) + a) Np + i]
+// (a fused launch draws its two O half-steps jointly from NS + 1 normals; the prologue
+// uses the first NS).  FP64
 // transcendental functions are the bulk of the FP64 path's work; this kernel spreads
 // them over the whole GPU while the integrator (one CTA per replica) stays small.
 // One thread per (it, r, Philox call k, i), i fastest, so the stores coalesce.
@@ -36,7 +38,8 @@ template <int NS>
 __global__ void __launch_bounds__(256)
 fp64_noise_kernel(uint32_t key0, uint32_t key1, uint32_t roff, int N, int Np, int R,
                   uint32_t kappa0, int iters, double* __restrict__ xi) {
-    constexpr int kCalls = (2 * NS + 3) / 4;
+    constexpr int kCount = NS + 1;
+    constexpr int kCalls = (kCount + 3) / 4;
     const int64_t total = (int64_t)iters * R * kCalls * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -48,13 +51,13 @@ fp64_noise_kernel(uint32_t key0, uint32_t key1, uint32_t roff, int N, int Np, in
         const int it = (int)(rest / R);
         const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i,
                                                  (uint32_t)r + roff, (uint32_t)k), key0, key1);
-        double* out = xi + ((int64_t)it * R + r) * (2 * NS) * Np + i;
+        double* out = xi + ((int64_t)it * R + r) * kCount * Np + i;
         double z[4];
         box_muller64(x.x, x.y, z[0], z[1]);
-        if (4 * k + 2 < 2 * NS) box_muller64(x.z, x.w, z[2], z[3]);
+        if (4 * k + 2 < kCount) box_muller64(x.z, x.w, z[2], z[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (4 * k + j < 2 * NS) out[(int64_t)(4 * k + j) * Np] = z[j];
+            if (4 * k + j < kCount) out[(int64_t)(4 * k + j) * Np] = z[j];
     }
 }
 
@@ -132,16 +135,19 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         }
         __syncthreads();   // all reads of qs done before it is overwritten
         if (i < N) {
-            double xi[2 * NS];
-            const double* nz = noise + ((int64_t)it * R + r) * (2 * NS) * Np + i;
+            double xi[NS + 1];
+            const double* nz = noise + ((int64_t)it * R + r) * (NS + 1) * Np + i;
 #pragma unroll
-            for (int a = 0; a < 2 * NS; ++a) xi[a] = nz[(int64_t)a * Np];
+            for (int a = 0; a < NS + 1; ++a) xi[a] = nz[(int64_t)a * Np];
             if (!pro) {
+                // end of the step, sample, start of the next: the two O half-steps jointly
                 v[0] = fma(-g.hdt, mq, v[0]);
+                double pmid;
+                o_joint<NS, double>(v, g, xi, pmid);
+                xs[i] = observable ? qi : pmid;
+            } else {
                 o_half<NS, double>(v, g.T, g.S, xi);
-                xs[i] = observable ? qi : v[0];
             }
-            o_half<NS, double>(v, g.T, g.S, xi + NS);
             v[0] = fma(-g.hdt, mq, v[0]);
             qi = fma(g.dt, v[0], qi);
             qs[i] = qi;
@@ -169,7 +175,7 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
                               uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st) {
     if (iters <= 0) return cudaSuccess;
-    const int64_t calls = (2 * ns + 3) / 4;
+    const int64_t calls = (ns + 1 + 3) / 4;
     const int64_t total = iters * R * calls * N;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
 #define FTH_F64N_CASE(NSV)                                                                  \

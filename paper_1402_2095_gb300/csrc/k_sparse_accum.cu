@@ -59,7 +59,7 @@ csr_step_kernel(GleF32 g, int N, int R, int Rp, const int32_t* __restrict__ rowp
         float v[NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
-        float xi[2 * NS];
+        float xi[NS + 1];
         gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.rk, xi);
         gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
 #pragma unroll

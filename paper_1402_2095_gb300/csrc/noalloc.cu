@@ -111,11 +111,7 @@ extern "C" fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t 
 
     const int ns = s_aux + 1;
     GleF32 g{};
-    for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b) {
-            g.T[a * kMaxNs + b] = (float)(T[a * ns + b] - (a == b ? 1.0 : 0.0));   // D = T - I
-            g.S[a * kMaxNs + b] = (float)S[a * ns + b];
-        }
+    fill_gle_constants(ns, T, S, &g, nullptr);   // D = T - I, S, joint factor
     g.dt = (float)dt;
     g.hdt = (float)(0.5 * dt);
     g.key0 = (uint32_t)seed;

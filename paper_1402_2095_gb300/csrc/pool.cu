@@ -471,11 +471,7 @@ fth_status fth_pool_add(fth_pool* P, const fth_matrix* M, const fth_gle* gle,
     pr.npairs = po->npairs;
     PoolDesc& d = pr.h;
     std::memset(&d, 0, sizeof d);
-    for (int a = 0; a < ns; ++a)
-        for (int b = 0; b < ns; ++b) {
-            d.g.T[a * kMaxNs + b] = (float)(T[a * ns + b] - (a == b ? 1.0 : 0.0));
-            d.g.S[a * kMaxNs + b] = (float)S[a * ns + b];
-        }
+    fill_gle_constants(ns, T, S, &d.g, nullptr);
     d.g.dt = (float)po->dt;
     d.g.hdt = (float)(0.5 * po->dt);
     d.g.key0 = (uint32_t)po->seed;

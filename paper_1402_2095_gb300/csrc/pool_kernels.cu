@@ -335,7 +335,7 @@ __device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, int i, int 
         float v[NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
-        float xi[2 * NS];
+        float xi[NS + 1];
         gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.g.roff, c.g.rk, xi);
         samp[e] = 0.f;
         gle_fused<NS>(qa[e], v, mqa[e], c.g, xi, c.flags, c.observable, samp[e]);
@@ -503,7 +503,7 @@ __device__ __forceinline__ void pool_csr_rows(const PoolDesc& d, int i, int r0, 
         float v[NS];
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
-        float xi[2 * NS];
+        float xi[NS + 1];
         gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + d.g.roff, d.g.rk, xi);
         gle_fused<NS>(qa[e], v, mqa[e], d.g, xi, flags, d.observable, samp[e]);
 #pragma unroll
