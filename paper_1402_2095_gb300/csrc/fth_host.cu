@@ -44,6 +44,7 @@ struct Layout {
     size_t off_M = 0, off_Mlo = 0, off_rowptr = 0, off_col = 0, off_val = 0;
     size_t off_q0 = 0, off_q1 = 0, off_p = 0, off_s = 0, off_MQ = 0, off_ophi = 0, off_oplo = 0;
     size_t off_ps = 0, off_ps1 = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
+    size_t off_prow = 0, off_pcol = 0, off_pe = 0;   // pairs grouped by row (FP32 list paths)
     size_t off_gidx = 0, off_gout = 0, off_err = 0;
     size_t off_xi = 0;       // FP64 path: normals of one segment
     int64_t xi_chunk = 0;    // kick indices per segment that the buffer holds
@@ -334,6 +335,11 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_xi = c.take(per * (size_t)L->xi_chunk);
     }
     L->off_pairs = c.take((size_t)std::max<int64_t>(ntracked, 1) * 2 * 4);
+    if (L->path != kPathDense64 && o->track != FTH_TRACK_ALL) {
+        L->off_prow = c.take((size_t)(L->N + 1) * 4);
+        L->off_pcol = c.take((size_t)std::max<int64_t>(ntracked, 1) * 4);
+        L->off_pe = c.take((size_t)std::max<int64_t>(ntracked, 1) * 4);
+    }
     if (L->path == kPathDense64) L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * L->R * 8);
     else L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * 4);
     L->off_mean = c.take((size_t)std::max<int64_t>(L->count, 1) * 8);
@@ -420,6 +426,9 @@ struct fth_ctx {
     TcSyrk* tcs1 = nullptr;
     // host-side bookkeeping
     std::unordered_map<uint64_t, int64_t> pair_index;
+    int32_t* prow = nullptr;   // tracked pairs grouped by first index (device)
+    int32_t* pcol = nullptr;
+    int32_t* pe = nullptr;
     // linear functionals (device storage owned by the caller)
     struct Functional {
         int64_t* idx;
@@ -549,6 +558,10 @@ fth_status accumulate(fth_ctx* c) {
                                         static_cast<float*>(c->partial), c->side),
                        "syrk");
             }
+        } else if (c->prow && pair_accum_rows_supported(ncols)) {
+            FTH_CK(launch_pair_accum_rows(c->psb[b], L.ps_ld, ncols, c->prow, c->pcol, c->pe, L.N,
+                                          static_cast<float*>(c->partial), c->side),
+                   "pair accumulate (rows)");
         } else {
             FTH_CK(launch_pair_accum(c->psb[b], L.ps_ld, ncols, c->pairs, L.ntracked,
                                      static_cast<float*>(c->partial), c->side),
@@ -886,6 +899,11 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     c->psb[1] = L.off_ps1 ? static_cast<float*>(at(L.off_ps1)) : nullptr;
     c->ps = c->psb[0];
     c->pairs = static_cast<int32_t*>(at(L.off_pairs));
+    if (L.off_prow) {
+        c->prow = static_cast<int32_t*>(at(L.off_prow));
+        c->pcol = static_cast<int32_t*>(at(L.off_pcol));
+        c->pe = static_cast<int32_t*>(at(L.off_pe));
+    }
     c->partial = at(L.off_partial);
     c->mean = static_cast<double*>(at(L.off_mean));
     c->m2 = static_cast<double*>(at(L.off_m2));
@@ -1056,6 +1074,26 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
         }
         if (!pr.empty()) {
             FTH_CK_C(cudaMemcpyAsync(c->pairs, pr.data(), pr.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d pairs");
+            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        }
+        if (c->prow) {
+            // the same pairs grouped by their first index (counting sort over rows)
+            const int64_t np = (int64_t)pr.size() / 2;
+            std::vector<int32_t> prow((size_t)N + 1, 0), pcol((size_t)std::max<int64_t>(np, 1)),
+                pe((size_t)std::max<int64_t>(np, 1));
+            for (int64_t e = 0; e < np; ++e) ++prow[pr[2 * e] + 1];
+            for (int64_t i = 0; i < N; ++i) prow[i + 1] += prow[i];
+            std::vector<int32_t> fill(prow.begin(), prow.end() - 1);
+            for (int64_t e = 0; e < np; ++e) {
+                const int32_t k = fill[pr[2 * e]]++;
+                pcol[k] = pr[2 * e + 1];
+                pe[k] = (int32_t)e;
+            }
+            FTH_CK_C(cudaMemcpyAsync(c->prow, prow.data(), prow.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d prow");
+            if (np) {
+                FTH_CK_C(cudaMemcpyAsync(c->pcol, pcol.data(), np * 4, cudaMemcpyHostToDevice, c->stream), "h2d pcol");
+                FTH_CK_C(cudaMemcpyAsync(c->pe, pe.data(), np * 4, cudaMemcpyHostToDevice, c->stream), "h2d pe");
+            }
             FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
         }
     }

@@ -110,6 +110,12 @@ __host__ __device__ inline int64_t packed_index(int64_t i, int64_t j, int64_t nb
     return tile * (int64_t)kTile * kTile + (i % kTile) * kTile + (j % kTile);
 }
 
+// Pair accumulation grouped by row (CSR of partners); ncols must be supported.
+bool pair_accum_rows_supported(int64_t ncols);
+cudaError_t launch_pair_accum_rows(const float* ps, int64_t ps_ld, int64_t ncols,
+                                   const int32_t* prow, const int32_t* pcol, const int32_t* pe,
+                                   int64_t N, float* partial, cudaStream_t st);
+
 // Linear functional of tracked elements: fold one completed block (see the kernel).
 cudaError_t launch_functional_block(const float* partial32, const double* partial64, int64_t R,
                                     int64_t stride, const int64_t* idx, const double* w,

@@ -133,6 +133,63 @@ cudaError_t launch_pair_accum(const float* ps, int64_t ps_ld, int64_t ncols,
     return cudaGetLastError();
 }
 
+// Row-grouped form: the tracked pairs sorted by their first index (CSR over rows:
+// prow[i] .. prow[i+1] list the partners pcol and accumulator slots pe of row i).  A
+// warp keeps row i of the staged samples in registers and streams its partners, so
+// each row is read once for its own pairs instead of once per pair; for stencil-like
+// pair lists (diagonal + lattice neighbours) the partner rows are near i and come
+// from L2.  V float4 per lane: ncols = 128 V.
+template <int V>
+__global__ void __launch_bounds__(256)
+pair_accum_rows_kernel(const float* __restrict__ ps, int64_t ps_ld, const int32_t* __restrict__ prow,
+                       const int32_t* __restrict__ pcol, const int32_t* __restrict__ pe, int N,
+                       float* __restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < N; i += nw) {
+        const int k0 = prow[i], k1 = prow[i + 1];
+        if (k0 == k1) continue;
+        float4 a[V];
+        const float4* ra = reinterpret_cast<const float4*>(ps + i * ps_ld);
+#pragma unroll
+        for (int v = 0; v < V; ++v) a[v] = ra[v * 32 + lane];
+        for (int k = k0; k < k1; ++k) {
+            const float4* rb = reinterpret_cast<const float4*>(ps + (int64_t)pcol[k] * ps_ld);
+            float acc = 0.f;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float4 b = rb[v * 32 + lane];
+                acc = fmaf(a[v].x, b.x, acc);
+                acc = fmaf(a[v].y, b.y, acc);
+                acc = fmaf(a[v].z, b.z, acc);
+                acc = fmaf(a[v].w, b.w, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) partial[pe[k]] += acc;
+        }
+    }
+}
+
+bool pair_accum_rows_supported(int64_t ncols) {
+    return ncols == 128 || ncols == 256 || ncols == 512 || ncols == 1024;
+}
+
+cudaError_t launch_pair_accum_rows(const float* ps, int64_t ps_ld, int64_t ncols,
+                                   const int32_t* prow, const int32_t* pcol, const int32_t* pe,
+                                   int64_t N, float* partial, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>((N * 32 + 255) / 256, 152 * 16);
+    switch (ncols) {
+        case 128: pair_accum_rows_kernel<1><<<blocks, 256, 0, st>>>(ps, ps_ld, prow, pcol, pe, (int)N, partial); break;
+        case 256: pair_accum_rows_kernel<2><<<blocks, 256, 0, st>>>(ps, ps_ld, prow, pcol, pe, (int)N, partial); break;
+        case 512: pair_accum_rows_kernel<4><<<blocks, 256, 0, st>>>(ps, ps_ld, prow, pcol, pe, (int)N, partial); break;
+        case 1024: pair_accum_rows_kernel<8><<<blocks, 256, 0, st>>>(ps, ps_ld, prow, pcol, pe, (int)N, partial); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- FP32 FFMA SYRK
 // tiles[t(I,J)][a][b] += sum_c ps[I*128+a][c] ps[J*128+b][c] for the upper tiles I <= J.
 // 256 threads, 8 x 8 outputs each, BK = 8.
