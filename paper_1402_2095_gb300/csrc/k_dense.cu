@@ -22,7 +22,7 @@ __device__ __forceinline__ float to_tf32(float x) {
 // transposed operand stores (q^T[r][i]) are coalesced, and every thread moves one
 // 16-byte vector per plane.
 template <int NS>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, int mq_planes,
                  float* __restrict__ q, float* __restrict__ p, float* __restrict__ s,
                  uint32_t kappa, int flags, int observable, float* __restrict__ ps,
