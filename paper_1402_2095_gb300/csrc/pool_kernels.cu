@@ -472,29 +472,43 @@ cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem
 }
 
 // ------------------------------------------------------------------ CSR fused step
+// Warp tasks as in the dense step: 4 rows x 32 replicas per pass, 8 lanes per row with 4
+// replicas each, so the state rows and every neighbour row q[j][r0 .. r0+3] a row's
+// lanes gather are whole 128-byte segments; the row's column indices and values are
+// broadcast loads.  Positions ping-pong between q[cur] and q[cur ^ 1].
+struct PoolCsrShared {
+    GleF32 g;
+    const float* qin;
+    float* qout;
+    float* p;
+    float* s;
+    float* x;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const float* val;
+    int n, ns, flags, observable, primed;
+    uint32_t kappa;
+};
+
 template <int NS>
-__device__ __forceinline__ void pool_csr_rows(const PoolDesc& d, int i, int r0, int RN) {
-    const size_t plane = (size_t)d.n * RN;
+__device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, int i, int r0, int RN) {
+    const size_t plane = (size_t)c.n * RN;
     const size_t off = (size_t)i * RN + r0;
-    const float* qin = d.q[d.cur];
-    float* qout = d.q[d.cur ^ 1];
     float4 mq4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int e1 = d.rowptr[i + 1];
-    for (int e = d.rowptr[i]; e < e1; ++e) {
-        const float m = d.val[e];
-        const float4 x = *reinterpret_cast<const float4*>(qin + (size_t)d.col[e] * RN + r0);
+    const int e1 = c.rowptr[i + 1];
+    for (int e = c.rowptr[i]; e < e1; ++e) {
+        const float m = c.val[e];
+        const float4 x = *reinterpret_cast<const float4*>(c.qin + (size_t)c.col[e] * RN + r0);
         mq4.x = fmaf(m, x.x, mq4.x);
         mq4.y = fmaf(m, x.y, mq4.y);
         mq4.z = fmaf(m, x.z, mq4.z);
         mq4.w = fmaf(m, x.w, mq4.w);
     }
-    float4 q4 = *reinterpret_cast<const float4*>(qin + off);
+    float4 q4 = *reinterpret_cast<const float4*>(c.qin + off);
     float4 v4[NS];
-    v4[0] = *reinterpret_cast<const float4*>(d.p + off);
+    v4[0] = *reinterpret_cast<const float4*>(c.p + off);
 #pragma unroll
-    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(d.s + (a - 1) * plane + off);
-    const int flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
-    const uint32_t kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(c.s + (a - 1) * plane + off);
     float* qa = reinterpret_cast<float*>(&q4);
     const float* mqa = reinterpret_cast<const float*>(&mq4);
     float samp[4] = {0.f, 0.f, 0.f, 0.f};
@@ -504,34 +518,63 @@ __device__ __forceinline__ void pool_csr_rows(const PoolDesc& d, int i, int r0, 
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[NS + 1];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + d.g.roff, d.g.rk, xi);
-        gle_fused<NS>(qa[e], v, mqa[e], d.g, xi, flags, d.observable, samp[e]);
+        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.g.roff, c.g.rk, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], c.g, xi, c.flags, c.observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
     }
-    *reinterpret_cast<float4*>(qout + off) = q4;
-    *reinterpret_cast<float4*>(d.p + off) = v4[0];
+    *reinterpret_cast<float4*>(c.qout + off) = q4;
+    *reinterpret_cast<float4*>(c.p + off) = v4[0];
 #pragma unroll
-    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(d.s + (a - 1) * plane + off) = v4[a];
-    if (d.primed)
-        *reinterpret_cast<float4*>(d.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
+    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(c.s + (a - 1) * plane + off) = v4[a];
+    if (c.primed)
+        *reinterpret_cast<float4*>(c.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
 }
 
 __global__ void __launch_bounds__(256, 2)
 pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
                 int nitems, int RN) {
-    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
-        const PoolRowItem it = items[j];
-        const PoolDesc& d = desc[it.problem];
-        const int i = it.row0 + threadIdx.x;
-        if (i >= d.n) continue;
-        for (int r0 = threadIdx.y * 4; r0 < RN; r0 += 32) {
-            switch (d.ns) {
-                case 1: pool_csr_rows<1>(d, i, r0, RN); break;
-                case 2: pool_csr_rows<2>(d, i, r0, RN); break;
-                case 3: pool_csr_rows<3>(d, i, r0, RN); break;
-                case 4: pool_csr_rows<4>(d, i, r0, RN); break;
-                default: pool_csr_rows<5>(d, i, r0, RN); break;
+    __shared__ PoolCsrShared cs[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PoolCsrShared& c = cs[warp];
+    const int gw = blockIdx.x * 8 + warp, nw = gridDim.x * 8;
+    int cur = -1;
+    for (int task = gw; task < nitems * 8; task += nw) {
+        const PoolRowItem it = items[task >> 3];
+        if (it.problem != cur) {
+            const PoolDesc& d = desc[it.problem];
+            __syncwarp();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.g);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&c.g);
+            for (int w = lane; w < (int)(sizeof(GleF32) / 4); w += 32) dst[w] = src[w];
+            if (lane == 0) {
+                c.qin = d.q[d.cur];
+                c.qout = d.q[d.cur ^ 1];
+                c.p = d.p;
+                c.s = d.s;
+                c.x = d.x;
+                c.rowptr = d.rowptr;
+                c.col = d.col;
+                c.val = d.val;
+                c.n = d.n;
+                c.ns = d.ns;
+                c.primed = d.primed;
+                c.flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
+                c.observable = d.observable;
+                c.kappa = (uint32_t)(d.primed ? d.t + 1 : d.t);
+            }
+            cur = it.problem;
+            __syncwarp();
+        }
+        const int i = it.row0 + (task & 7) * 4 + (lane >> 3);
+        if (i >= c.n) continue;
+        for (int r0 = (lane & 7) * 4; r0 < RN; r0 += 32) {
+            switch (c.ns) {
+                case 1: pool_csr_quad<1>(c, i, r0, RN); break;
+                case 2: pool_csr_quad<2>(c, i, r0, RN); break;
+                case 3: pool_csr_quad<3>(c, i, r0, RN); break;
+                case 4: pool_csr_quad<4>(c, i, r0, RN); break;
+                default: pool_csr_quad<5>(c, i, r0, RN); break;
             }
         }
     }
@@ -540,8 +583,15 @@ pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
 cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
                             cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    const int grid = std::min(nitems, 152 * 12);
-    pool_csr_kernel<<<grid, dim3(32, 8), 0, st>>>(desc, items, nitems, RN);
+    static const int resident = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_csr_kernel, 256, 0);
+        return std::max(1, sms * std::max(per, 1));
+    }();
+    const int grid = std::min(nitems, resident);
+    pool_csr_kernel<<<grid, 256, 0, st>>>(desc, items, nitems, RN);
     return cudaGetLastError();
 }
 

@@ -375,3 +375,25 @@ def test_functional_fp64_dense_operator():
     vo, eo = _functional_from_samples(samples, 0, 25, p, w)
     assert abs(v - vo) <= 1e-10 * abs(vo)
     assert abs(e - eo) <= 1e-8 * eo
+
+
+def test_functional_dense_all_elements_tf32_tiles():
+    """Functionals over the tile-packed all-elements accumulators of the tensor-core path
+    (SYRK on the side stream, block fold before the flush)."""
+    from paper_1402_2095_gb300.binding import trace_terms
+    n = 200
+    M = _dense(n, seed=71)
+    a, c = syn.random_gle(4, seed=72, rate=3.0)
+    g, o = make_pair(M, a_p=a, c_p=c, dt=0.01, R=64, seed=73, precision="bf16x3", track="all",
+                     burnin=10, block=30, M_oracle=M)
+    p, w = trace_terms(O=M)
+    fid = g.add_functional(p, w)
+    tid = g.add_functional(*trace_terms(n=n))
+    g.run(310)
+    samples = o.run(310, keep_samples=True)
+    for f_id, (pp, ww) in ((fid, (p, w)), (tid, trace_terms(n=n))):
+        v, e = g.functional(f_id)
+        vo, eo = _functional_from_samples(samples, 10, 30, pp, ww)
+        # BF16x3 force: trajectories agree to ~3e-4 of their scale
+        assert abs(v - vo) <= 2e-3 * abs(vo)
+        assert abs(e - eo) <= 2e-2 * eo

@@ -186,3 +186,26 @@ def test_pool_rejects_invalid_problems():
     with pytest.raises(FthError):
         pool.add(_dense(8, seed=62), a_p=a, c_p=c, dt=0.01, pairs=[(0, 8)])
     assert pool.stats()["live"] == 0 and pool.stats()["used_bytes"] == 0
+
+
+def test_pool_graph_recaptured_after_membership_change():
+    """A problem added after a graph was captured joins the next graph; every problem
+    still matches its oracle (the graph reads the rebuilt work lists)."""
+    pool = _pool(replicas=32, graph_steps=10)
+    M1 = _dense(150, seed=80)
+    a, c = _gle(4, 81)
+    h1 = pool.add(M1, a_p=a, c_p=c, dt=0.01, seed=5)
+    o1 = OracleFTH(M=M1, a_p=a, c_p=c, dt=0.01, replicas=32, seed=5)
+    pool.run(1 + 40)
+    o1.run(40)
+    M2 = _dense(90, seed=82)
+    h2 = pool.add(M2, a_p=a, c_p=c, dt=0.01, seed=6)
+    o2 = OracleFTH(M=M2, a_p=a, c_p=c, dt=0.01, replicas=32, seed=6)
+    pool.run(1 + 39)
+    o1.run(40)
+    o2.run(39)
+    assert pool.stats()["graphs"] >= 2
+    for h, o in ((h1, o1), (h2, o2)):
+        for name, ref in (("q", o.q), ("p", o.p)):
+            got = pool.get_state(h, name)
+            assert np.max(np.abs(got - ref)) <= 3e-4 * np.max(np.abs(ref))
