@@ -106,8 +106,23 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
     __syncthreads();
     double* acc = p_smem ? pacc : gacc;
     const int32_t* pr = p_smem ? pidx : pairs;
+    // the normals of the next iteration are loaded while this one computes
+    double xn[NS + 1];
+    if (i < N) {
+        const double* nz = noise + (int64_t)r * (NS + 1) * Np + i;
+#pragma unroll
+        for (int a = 0; a < NS + 1; ++a) xn[a] = nz[(int64_t)a * Np];
+    }
     for (int it = 0; it < iters; ++it) {
         const bool pro = prologue && it == 0;
+        double xi[NS + 1];
+#pragma unroll
+        for (int a = 0; a < NS + 1; ++a) xi[a] = xn[a];
+        if (i < N && it + 1 < iters) {
+            const double* nz = noise + ((int64_t)(it + 1) * R + r) * (NS + 1) * Np + i;
+#pragma unroll
+            for (int a = 0; a < NS + 1; ++a) xn[a] = nz[(int64_t)a * Np];
+        }
         double mq = 0.0;
         if (i < N) {
             // four independent partial sums: the FP64 latency chain is a quarter as long
@@ -135,10 +150,6 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         }
         __syncthreads();   // all reads of qs done before it is overwritten
         if (i < N) {
-            double xi[NS + 1];
-            const double* nz = noise + ((int64_t)it * R + r) * (NS + 1) * Np + i;
-#pragma unroll
-            for (int a = 0; a < NS + 1; ++a) xi[a] = nz[(int64_t)a * Np];
             if (!pro) {
                 // end of the step, sample, start of the next: the two O half-steps jointly
                 v[0] = fma(-g.hdt, mq, v[0]);
@@ -155,6 +166,7 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         __syncthreads();
         const int f = prologue ? it - 1 : it;   // index of this fused launch in the segment
         if (!pro && f >= acc_from) {
+#pragma unroll 4
             for (int e = i; e < npairs; e += blockDim.x)
                 acc[e] = fma(xs[pr[2 * e]], xs[pr[2 * e + 1]], acc[e]);
         }
@@ -169,6 +181,134 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         p[base + i] = v[0];
 #pragma unroll
         for (int a = 1; a < NS; ++a) s[(a - 1) * plane + base + i] = v[a];
+    }
+}
+
+// Small problems (N <= 32): the FP64 units of an SM sit in its four sub-partitions and a
+// warp issues to one of them, so one warp per replica uses a quarter of the SM's FP64
+// rate.  Here four warps share each replica's work: warp w forms the force over columns
+// k = 8w .. 8w+7 and a quarter of the O-step outputs (pmid and out[0..NS) are NS + 1
+// rows of the joint update, output o to warp o % 4); lane = dof.  State in shared
+// memory, double-buffered between steps; two barriers per step.
+template <int NS>
+__global__ void __launch_bounds__(128)
+fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double* __restrict__ q,
+                  double* __restrict__ p, double* __restrict__ s, const double* __restrict__ noise,
+                  int iters, int prologue, int observable, const int32_t* __restrict__ pairs,
+                  int npairs, double* __restrict__ partial, int acc_from) {
+    extern __shared__ double sh[];
+    double* qs = sh;                              // [32]
+    double* xs = qs + 32;                         // [32]
+    double* fpart = xs + 32;                      // [4][32]
+    double* vs = fpart + 4 * 32;                  // [2][NS][32]
+    double* mt = vs + 2 * NS * 32;                // [32][32] (M transposed)
+    double* pacc = mt + 32 * 32;                  // [npairs]
+    int32_t* pidx = reinterpret_cast<int32_t*>(pacc + npairs);
+    const int r = blockIdx.x, R = gridDim.x;
+    const int warp = threadIdx.x >> 5, i = threadIdx.x & 31, tid = threadIdx.x;
+    const int64_t base = (int64_t)r * Np;
+    const int64_t plane = (int64_t)R * Np;
+    double* gacc = partial + (int64_t)r * npairs;
+    if (warp == 0) {
+        qs[i] = i < N ? q[base + i] : 0.0;
+        vs[i] = i < N ? p[base + i] : 0.0;
+#pragma unroll
+        for (int a = 1; a < NS; ++a) vs[a * 32 + i] = i < N ? s[(a - 1) * plane + base + i] : 0.0;
+    }
+    for (int e = tid; e < 32 * 32; e += 128) {
+        const int row = e / 32, k = e % 32;
+        mt[k * 32 + row] = (row < N && k < N) ? M[(int64_t)row * Np + k] : 0.0;
+    }
+    for (int e = tid; e < npairs; e += 128) {
+        pacc[e] = gacc[e];
+        pidx[2 * e] = pairs[2 * e];
+        pidx[2 * e + 1] = pairs[2 * e + 1];
+    }
+    double zn[NS + 1];
+    {
+        const double* nz = noise + (int64_t)r * (NS + 1) * Np + (i < N ? i : 0);
+#pragma unroll
+        for (int a = 0; a < NS + 1; ++a) zn[a] = nz[(int64_t)a * Np];
+    }
+    __syncthreads();
+    int cb = 0;
+    for (int it = 0; it < iters; ++it) {
+        const bool pro = prologue && it == 0;
+        double z[NS + 1];
+#pragma unroll
+        for (int a = 0; a < NS + 1; ++a) z[a] = zn[a];
+        if (it + 1 < iters) {
+            const double* nz = noise + ((int64_t)(it + 1) * R + r) * (NS + 1) * Np + (i < N ? i : 0);
+#pragma unroll
+            for (int a = 0; a < NS + 1; ++a) zn[a] = nz[(int64_t)a * Np];
+        }
+        // force, a quarter of the columns per warp
+        {
+            double f0 = 0.0, f1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                f0 = fma(mt[(warp * 8 + k) * 32 + i], qs[warp * 8 + k], f0);
+                f1 = fma(mt[(warp * 8 + k + 1) * 32 + i], qs[warp * 8 + k + 1], f1);
+            }
+            fpart[warp * 32 + i] = f0 + f1;
+        }
+        __syncthreads();
+        const double mq = (fpart[i] + fpart[32 + i]) + (fpart[64 + i] + fpart[96 + i]);
+        const double* vc = vs + cb * NS * 32;
+        double* vn = vs + (cb ^ 1) * NS * 32;
+        double v[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) v[a] = vc[a * 32 + i];
+        if (!pro) v[0] = fma(-g.hdt, mq, v[0]);   // B(dt/2), end of the step (not in the prologue)
+#pragma unroll
+        for (int o = 0; o <= NS; ++o) {
+            if ((o & 3) != warp) continue;
+            if (o == 0) {
+                if (!pro) {
+                    double u = g.L[0] * z[0];
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) u = fma(g.T[b], v[b], u);
+                    if (!observable) xs[i] = v[0] + u;
+                }
+                continue;
+            }
+            const int a = o - 1;
+            double acc = 0.0;
+            if (pro) {
+#pragma unroll
+                for (int b = 0; b < NS; ++b) acc = fma(g.T[a * kMaxNs + b], v[b], acc);
+#pragma unroll
+                for (int b = 0; b <= a; ++b) acc = fma(g.S[a * kMaxNs + b], z[b], acc);
+            } else {
+#pragma unroll
+                for (int b = 0; b < NS; ++b) acc = fma(g.D2[a * kMaxNs + b], v[b], acc);
+#pragma unroll
+                for (int b = 0; b <= a + 1; ++b) acc = fma(g.L[(a + 1) * kMaxNs1 + b], z[b], acc);
+            }
+            double va = v[a] + acc;
+            if (a == 0) {
+                // B(dt/2) and A(dt) of the next step; the sample of q is the position before A
+                va = fma(-g.hdt, mq, va);
+                const double qold = qs[i];
+                if (!pro && observable) xs[i] = qold;
+                qs[i] = fma(g.dt, va, qold);
+            }
+            vn[a * 32 + i] = va;
+        }
+        __syncthreads();
+        const int f = prologue ? it - 1 : it;
+        if (!pro && f >= acc_from)
+            for (int e = tid; e < npairs; e += 128)
+                pacc[e] = fma(xs[pidx[2 * e]], xs[pidx[2 * e + 1]], pacc[e]);
+        cb ^= 1;
+    }
+    __syncthreads();
+    for (int e = tid; e < npairs; e += 128) gacc[e] = pacc[e];
+    if (warp == 0 && i < N) {
+        q[base + i] = qs[i];
+        p[base + i] = vs[cb * NS * 32 + i];
+#pragma unroll
+        for (int a = 1; a < NS; ++a) s[(a - 1) * plane + base + i] = vs[cb * NS * 32 + a * 32 + i];
     }
 }
 
@@ -203,9 +343,31 @@ cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, in
     const int prologue = primed_in ? 0 : 1;
     const int iters = (int)nsteps + prologue;
     if (iters <= 0) return cudaSuccess;
+    constexpr size_t kBudget = 200 * 1024;
+    const size_t small_bytes = sizeof(double) * (32 * 6 + 2 * (size_t)ns * 32 + 32 * 32) +
+                               (size_t)npairs * 16;
+    if (N <= 32 && small_bytes <= kBudget) {
+#define FTH_F64S_CASE(NSV)                                                                  \
+    case NSV:                                                                               \
+        cudaFuncSetAttribute(fp64_small_kernel<NSV>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);    \
+        fp64_small_kernel<NSV><<<(unsigned)R, 128, small_bytes, st>>>(                      \
+            g, (int)N, (int)Np, M, q, p, s, noise, iters, prologue, observable, pairs,      \
+            (int)npairs, partial, (int)acc_from);                                           \
+        break;
+        switch (ns) {
+            FTH_F64S_CASE(1)
+            FTH_F64S_CASE(2)
+            FTH_F64S_CASE(3)
+            FTH_F64S_CASE(4)
+            FTH_F64S_CASE(5)
+            default: return cudaErrorInvalidValue;
+        }
+#undef FTH_F64S_CASE
+        return cudaGetLastError();
+    }
     const int threads = (int)std::max<int64_t>(32, ((N + 31) / 32) * 32);
     // shared memory: q and x always; then the pairs (16 B each) and M when they fit
-    constexpr size_t kBudget = 200 * 1024;
     size_t shmem = sizeof(double) * 2 * (size_t)Np;
     const size_t pbytes = (size_t)npairs * 16, mbytes = (size_t)N * Np * 8;
     const int p_smem = shmem + pbytes <= kBudget ? 1 : 0;

@@ -57,7 +57,7 @@ def test_csr_trajectory(L, R):
     assert _trajectory(g, o, 1000, 4) <= 1e-5
 
 
-@pytest.mark.parametrize("n,R", [(32, 16), (45, 3)])
+@pytest.mark.parametrize("n,R", [(32, 16), (45, 3), (20, 5), (1, 2)])
 def test_fp64_trajectory(n, R):
     a, c = syn.random_gle(4, seed=13, rate=3.0)
     g, o = make_pair(_dense(n), a_p=a, c_p=c, dt=0.01, R=R, seed=99, precision="fp64")
