@@ -740,9 +740,12 @@ pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ i
             }
             d.partial[e] += acc0 + acc1;
         }
-        __threadfence();
+        // the barrier orders every thread's partial store before thread 0's gpu-scope
+        // fence, which releases them all before the completion count (the pattern of a
+        // grid-wide barrier)
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             s_last = atomicAdd(&d.done, 1) == it.nchunks - 1;
             s_flush = 0;
             if (s_last) {
