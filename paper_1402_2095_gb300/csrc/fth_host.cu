@@ -306,8 +306,7 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_q0 = c.take((size_t)Np * Rp * 4);
         L->off_p = c.take((size_t)Np * Rp * 4);
         L->off_s = c.take((size_t)std::max(nsub, 1) * Np * Rp * 4);
-        // the tensor-core force may write up to kMaxForcePlanes partial planes
-        L->off_MQ = c.take((size_t)(tc ? kMaxForcePlanes : 1) * Np * Rp * 4);
+        L->off_MQ = c.take((size_t)Np * Rp * 4);
         if (tc) {
             L->off_ophi = c.take((size_t)Rp * Np * esz);
             if (o->precision == FTH_PREC_BF16X3) L->off_oplo = c.take((size_t)Rp * Np * esz);
@@ -619,7 +618,8 @@ fth_status flush(fth_ctx* c) {
     return FTH_OK;
 }
 
-int mq_planes(const fth_ctx* c) { return c->tcf ? tc_force_planes(c->tcf) : 1; }
+// The force arrives as one plane (the split-K kernel reduces its K shares on chip).
+int mq_planes(const fth_ctx*) { return 1; }
 
 void op_ptrs(fth_ctx* c, int& kind, void*& hi, void*& lo) {
     kind = kOpNone;

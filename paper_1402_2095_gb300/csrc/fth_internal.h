@@ -145,9 +145,6 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st);
 void tc_force_free(TcForce* tf);
-// Number of partial planes MQ[0..planes) the force kernel writes (summed by the GLE kernel).
-int tc_force_planes(const TcForce* tf);
-constexpr int kMaxForcePlanes = 4;
 
 struct TcSyrk;
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);

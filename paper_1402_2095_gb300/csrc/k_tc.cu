@@ -515,7 +515,6 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
                               nslices, err);
 }
 
-int tc_force_planes(const TcForce*) { return 1; }
 
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st) {
