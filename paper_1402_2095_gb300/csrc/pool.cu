@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <string>
@@ -109,6 +110,13 @@ struct fth_pool {
     std::vector<PoolAccItem> h_acc;
     std::vector<int> h_live;
     int64_t n_force = 0, n_dense_rows = 0, n_csr_rows = 0;
+    // row items grouped by shared GLE constants: one GLE (and one CSR) launch per group
+    struct Group {
+        GleF32 g;
+        int ns;
+        int64_t dense_begin, dense_count, csr_begin, csr_count;
+    };
+    std::vector<Group> groups;
     bool dirty = true;
     bool tuned = false;
     int variant = 0, grid = 152;
@@ -193,7 +201,20 @@ fth_status rebuild_lists(fth_pool* P) {
     P->h_rows.clear();
     P->h_live.clear();
     P->h_acc.clear();
-    std::vector<PoolRowItem> csr_rows;
+    P->groups.clear();
+    // the GLE constants of a problem up to (not including) its noise keys
+    const size_t key_bytes = offsetof(GleF32, key0);
+    auto group_of = [&](const PoolDesc& d) {
+        for (size_t k = 0; k < P->groups.size(); ++k)
+            if (P->groups[k].ns == d.ns && std::memcmp(&P->groups[k].g, &d.g, key_bytes) == 0)
+                return (int)k;
+        fth_pool::Group gr{};
+        gr.g = d.g;
+        gr.ns = d.ns;
+        P->groups.push_back(gr);
+        return (int)P->groups.size() - 1;
+    };
+    std::vector<std::vector<PoolRowItem>> dense_by(0), csr_by(0);
     for (int b = 0; b < (int)P->probs.size(); ++b) {
         const Problem& pr = P->probs[b];
         if (!pr.used) continue;
@@ -203,12 +224,26 @@ fth_status rebuild_lists(fth_pool* P) {
         const int nch = std::max(1, (np + kPoolAccChunk - 1) / kPoolAccChunk);
         for (int c = 0; c < nch; ++c)
             P->h_acc.push_back({b, c * kPoolAccChunk, std::min(np, (c + 1) * kPoolAccChunk), nch});
+        const int gi = group_of(pr.h);
+        dense_by.resize(P->groups.size());
+        csr_by.resize(P->groups.size());
         if (pr.h.kind == 0) {
             for (int rb = 0; rb < (n + 127) / 128; ++rb) P->h_force.push_back({b, rb});
-            for (int r0 = 0; r0 < n; r0 += 32) P->h_rows.push_back({b, r0});
+            for (int r0 = 0; r0 < n; r0 += 32) dense_by[gi].push_back({b, r0});
         } else {
-            for (int r0 = 0; r0 < n; r0 += 32) csr_rows.push_back({b, r0});
+            for (int r0 = 0; r0 < n; r0 += 32) csr_by[gi].push_back({b, r0});
         }
+    }
+    for (size_t k = 0; k < P->groups.size(); ++k) {
+        P->groups[k].dense_begin = (int64_t)P->h_rows.size();
+        P->groups[k].dense_count = (int64_t)dense_by[k].size();
+        P->h_rows.insert(P->h_rows.end(), dense_by[k].begin(), dense_by[k].end());
+    }
+    const int64_t n_dense = (int64_t)P->h_rows.size();
+    for (size_t k = 0; k < P->groups.size(); ++k) {
+        P->groups[k].csr_begin = (int64_t)P->h_rows.size();
+        P->groups[k].csr_count = (int64_t)csr_by[k].size();
+        P->h_rows.insert(P->h_rows.end(), csr_by[k].begin(), csr_by[k].end());
     }
     // longest K first, then round-robin over the persistent CTAs (LPT-like balance)
     std::stable_sort(P->h_force.begin(), P->h_force.end(),
@@ -216,9 +251,8 @@ fth_status rebuild_lists(fth_pool* P) {
                          return P->probs[a.problem].h.np > P->probs[b.problem].h.np;
                      });
     P->n_force = (int64_t)P->h_force.size();
-    P->n_dense_rows = (int64_t)P->h_rows.size();
-    P->n_csr_rows = (int64_t)csr_rows.size();
-    P->h_rows.insert(P->h_rows.end(), csr_rows.begin(), csr_rows.end());
+    P->n_dense_rows = n_dense;
+    P->n_csr_rows = (int64_t)P->h_rows.size() - n_dense;
     if (P->n_force > P->cap_force || (int64_t)P->h_rows.size() > P->cap_rows ||
         (int64_t)P->h_acc.size() > P->cap_acc)
         return perr(P, FTH_E_WORKSPACE, "work lists exceed the pool's capacity");
@@ -254,14 +288,19 @@ fth_status enqueue_step(fth_pool* P, cudaEvent_t* ev = nullptr) {
     }
     if (P->n_dense_rows > 0) {
         PCK(mark(FTH_PK_GLE, 0), "event");
-        PCK(launch_pool_gle(P->gle_variant, P->d_desc, P->d_rows, (int)P->n_dense_rows,
-                            (int)P->R, P->kind_tc, P->stream), "pool gle");
+        for (const auto& gr : P->groups)
+            if (gr.dense_count > 0)
+                PCK(launch_pool_gle(P->gle_variant, P->d_desc, P->d_rows + gr.dense_begin,
+                                    (int)gr.dense_count, (int)P->R, P->kind_tc, gr.ns, gr.g,
+                                    P->stream), "pool gle");
         PCK(mark(FTH_PK_GLE, 1), "event");
     }
     if (P->n_csr_rows > 0) {
         PCK(mark(FTH_PK_CSR, 0), "event");
-        PCK(launch_pool_csr(P->d_desc, P->d_rows + P->n_dense_rows, (int)P->n_csr_rows, (int)P->R,
-                            P->stream), "pool csr");
+        for (const auto& gr : P->groups)
+            if (gr.csr_count > 0)
+                PCK(launch_pool_csr(P->d_desc, P->d_rows + gr.csr_begin, (int)gr.csr_count,
+                                    (int)P->R, gr.ns, gr.g, P->stream), "pool csr");
         PCK(mark(FTH_PK_CSR, 1), "event");
     }
     PCK(mark(FTH_PK_ACCUM, 0), "event");

@@ -78,9 +78,10 @@ cudaError_t launch_pool_progress(const PoolDesc* desc, const int* live, int nliv
 constexpr size_t kPoolStageBytes = size_t(16) << 20;   // host-to-device staging of M rows
 constexpr int kPoolGleVariants = 3;
 cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
-                            int nitems, int RN, int kind, cudaStream_t st);
-cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            int nitems, int RN, int kind, int ns, const GleF32& gk,
                             cudaStream_t st);
+cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            int ns, const GleF32& gk, cudaStream_t st);
 cudaError_t launch_pool_accum(PoolDesc* desc, const PoolAccItem* items, int nitems, int RN,
                               uint32_t* err, cudaStream_t st);
 

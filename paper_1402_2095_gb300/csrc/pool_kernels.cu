@@ -296,8 +296,12 @@ __device__ __forceinline__ float to_tf32_pool(float x) {
     return __uint_as_float(r);
 }
 
+// Per-warp copy of a problem's fields; the GLE constants every problem of a launch
+// shares come as the kernel parameter `gk` (constant bank), only the noise keys and
+// the replica offset are per problem.
 struct PoolGleShared {
-    GleF32 g;
+    uint32_t rk[20];
+    uint32_t roff;
     float* q;
     float* p;
     float* s;
@@ -305,7 +309,7 @@ struct PoolGleShared {
     float* x;
     uint8_t* bt_hi;
     uint8_t* bt_lo;
-    int n, ns, flags, observable, primed;
+    int n, flags, observable, primed;
     uint32_t kappa;
 };
 
@@ -315,8 +319,8 @@ template <> struct VecF<4> { using T = float4; };
 
 // NE consecutive replicas r0 .. r0 + NE - 1 of row i.
 template <int NS, int NE>
-__device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, int i, int r0, int RN,
-                                             float (&qout)[NE]) {
+__device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, const GleF32& gk, int i,
+                                             int r0, int RN, float (&qout)[NE]) {
     using V = typename VecF<NE>::T;
     const size_t plane = (size_t)c.n * RN;
     const size_t off = (size_t)i * RN + r0;
@@ -336,9 +340,9 @@ __device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, int i, int 
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[NS + 1];
-        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.g.roff, c.g.rk, xi);
+        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xi);
         samp[e] = 0.f;
-        gle_fused<NS>(qa[e], v, mqa[e], c.g, xi, c.flags, c.observable, samp[e]);
+        gle_fused<NS>(qa[e], v, mqa[e], gk, xi, c.flags, c.observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
         qout[e] = qa[e];
@@ -351,10 +355,10 @@ __device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, int i, int 
 }
 
 // NE replicas per lane, MINB CTAs of 256 per SM (the register budget).
-template <int NE, int MINB>
+template <int NE, int MINB, int NS>
 __global__ void __launch_bounds__(256, MINB)
 pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
-                int nitems, int RN, int kind) {
+                int nitems, int RN, int kind, const GleF32 gk) {
     constexpr int LPR = 32 / NE;          // lanes per row: NE replicas each, 32 per pass
     __shared__ PoolGleShared cs[8];
     __shared__ __align__(16) float sq[8][4 * 32];
@@ -368,10 +372,9 @@ pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
         if (it.problem != cur) {
             const PoolDesc& d = desc[it.problem];
             __syncwarp();
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.g);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&c.g);
-            for (int w = lane; w < (int)(sizeof(GleF32) / 4); w += 32) dst[w] = src[w];
+            if (lane < 20) c.rk[lane] = d.g.rk[lane];
             if (lane == 0) {
+                c.roff = d.g.roff;
                 c.q = d.q[0];
                 c.p = d.p;
                 c.s = d.s;
@@ -380,7 +383,6 @@ pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
                 c.bt_hi = d.bt_hi;
                 c.bt_lo = d.bt_lo;
                 c.n = d.n;
-                c.ns = d.ns;
                 c.primed = d.primed;
                 c.flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
                 c.observable = d.observable;
@@ -399,15 +401,7 @@ pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
                 float qn[NE];
 #pragma unroll
                 for (int e = 0; e < NE; ++e) qn[e] = 0.f;
-                if (i < c.n) {
-                    switch (c.ns) {
-                        case 1: pool_gle_vec<1, NE>(c, i, r0, RN, qn); break;
-                        case 2: pool_gle_vec<2, NE>(c, i, r0, RN, qn); break;
-                        case 3: pool_gle_vec<3, NE>(c, i, r0, RN, qn); break;
-                        case 4: pool_gle_vec<4, NE>(c, i, r0, RN, qn); break;
-                        default: pool_gle_vec<5, NE>(c, i, r0, RN, qn); break;
-                    }
-                }
+                if (i < c.n) pool_gle_vec<NS, NE>(c, gk, i, r0, RN, qn);
 #pragma unroll
                 for (int e = 0; e < NE; ++e) tq[k * 32 + (lane % LPR) * NE + e] = qn[e];
             }
@@ -441,32 +435,47 @@ pool_gle_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
     }
 }
 
-template <int NE, int MINB>
+template <int NE, int MINB, int NS>
 cudaError_t launch_pool_gle_t(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
-                              int kind, cudaStream_t st) {
+                              int kind, const GleF32& gk, cudaStream_t st) {
     // persistent: one wave of resident CTAs walks the task list
     static const int resident = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_gle_kernel<NE, MINB>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_gle_kernel<NE, MINB, NS>, 256, 0);
         return std::max(1, sms * std::max(per, 1));
     }();
     const int grid = std::min(nitems, resident);
-    pool_gle_kernel<NE, MINB><<<grid, 256, 0, st>>>(desc, items, nitems, RN, kind);
+    pool_gle_kernel<NE, MINB, NS><<<grid, 256, 0, st>>>(desc, items, nitems, RN, kind, gk);
     return cudaGetLastError();
+}
+
+template <int NS>
+cudaError_t launch_pool_gle_ns(int variant, const PoolDesc* desc, const PoolRowItem* items,
+                               int nitems, int RN, int kind, const GleF32& gk, cudaStream_t st) {
+    switch (variant) {
+        case 0: return launch_pool_gle_t<4, 2, NS>(desc, items, nitems, RN, kind, gk, st);
+        case 1: return launch_pool_gle_t<2, 3, NS>(desc, items, nitems, RN, kind, gk, st);
+        case 2: return launch_pool_gle_t<4, 3, NS>(desc, items, nitems, RN, kind, gk, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Variants (replicas per lane, CTAs per SM): every variant runs the same arithmetic per
 // element, so they give identical results and the pool may time them on real steps.
+// One launch covers the problems that share the GLE constants `gk` (ns of them).
 cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
-                            int nitems, int RN, int kind, cudaStream_t st) {
+                            int nitems, int RN, int kind, int ns, const GleF32& gk,
+                            cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     if (RN > kPoolMaxRN || (RN & 31)) return cudaErrorInvalidValue;
-    switch (variant) {
-        case 0: return launch_pool_gle_t<4, 2>(desc, items, nitems, RN, kind, st);
-        case 1: return launch_pool_gle_t<2, 3>(desc, items, nitems, RN, kind, st);
-        case 2: return launch_pool_gle_t<2, 4>(desc, items, nitems, RN, kind, st);
+    switch (ns) {
+        case 1: return launch_pool_gle_ns<1>(variant, desc, items, nitems, RN, kind, gk, st);
+        case 2: return launch_pool_gle_ns<2>(variant, desc, items, nitems, RN, kind, gk, st);
+        case 3: return launch_pool_gle_ns<3>(variant, desc, items, nitems, RN, kind, gk, st);
+        case 4: return launch_pool_gle_ns<4>(variant, desc, items, nitems, RN, kind, gk, st);
+        case 5: return launch_pool_gle_ns<5>(variant, desc, items, nitems, RN, kind, gk, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -477,7 +486,8 @@ cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem
 // lanes gather are whole 128-byte segments; the row's column indices and values are
 // broadcast loads.  Positions ping-pong between q[cur] and q[cur ^ 1].
 struct PoolCsrShared {
-    GleF32 g;
+    uint32_t rk[20];
+    uint32_t roff;
     const float* qin;
     float* qout;
     float* p;
@@ -486,12 +496,13 @@ struct PoolCsrShared {
     const int32_t* rowptr;
     const int32_t* col;
     const float* val;
-    int n, ns, flags, observable, primed;
+    int n, flags, observable, primed;
     uint32_t kappa;
 };
 
 template <int NS>
-__device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, int i, int r0, int RN) {
+__device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, const GleF32& gk, int i,
+                                              int r0, int RN) {
     const size_t plane = (size_t)c.n * RN;
     const size_t off = (size_t)i * RN + r0;
     float4 mq4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -518,8 +529,8 @@ __device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, int i, int
 #pragma unroll
         for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
         float xi[NS + 1];
-        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.g.roff, c.g.rk, xi);
-        gle_fused<NS>(qa[e], v, mqa[e], c.g, xi, c.flags, c.observable, samp[e]);
+        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xi);
+        gle_fused<NS>(qa[e], v, mqa[e], gk, xi, c.flags, c.observable, samp[e]);
 #pragma unroll
         for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
     }
@@ -531,9 +542,10 @@ __device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, int i, int
         *reinterpret_cast<float4*>(c.x + off) = make_float4(samp[0], samp[1], samp[2], samp[3]);
 }
 
+template <int NS>
 __global__ void __launch_bounds__(256, 2)
 pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
-                int nitems, int RN) {
+                int nitems, int RN, const GleF32 gk) {
     __shared__ PoolCsrShared cs[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     PoolCsrShared& c = cs[warp];
@@ -544,10 +556,9 @@ pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
         if (it.problem != cur) {
             const PoolDesc& d = desc[it.problem];
             __syncwarp();
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&d.g);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&c.g);
-            for (int w = lane; w < (int)(sizeof(GleF32) / 4); w += 32) dst[w] = src[w];
+            if (lane < 20) c.rk[lane] = d.g.rk[lane];
             if (lane == 0) {
+                c.roff = d.g.roff;
                 c.qin = d.q[d.cur];
                 c.qout = d.q[d.cur ^ 1];
                 c.p = d.p;
@@ -557,7 +568,6 @@ pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
                 c.col = d.col;
                 c.val = d.val;
                 c.n = d.n;
-                c.ns = d.ns;
                 c.primed = d.primed;
                 c.flags = d.primed ? (kDoEnd | kDoStart) : kDoStart;
                 c.observable = d.observable;
@@ -568,31 +578,36 @@ pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict
         }
         const int i = it.row0 + (task & 7) * 4 + (lane >> 3);
         if (i >= c.n) continue;
-        for (int r0 = (lane & 7) * 4; r0 < RN; r0 += 32) {
-            switch (c.ns) {
-                case 1: pool_csr_quad<1>(c, i, r0, RN); break;
-                case 2: pool_csr_quad<2>(c, i, r0, RN); break;
-                case 3: pool_csr_quad<3>(c, i, r0, RN); break;
-                case 4: pool_csr_quad<4>(c, i, r0, RN); break;
-                default: pool_csr_quad<5>(c, i, r0, RN); break;
-            }
-        }
+        for (int r0 = (lane & 7) * 4; r0 < RN; r0 += 32) pool_csr_quad<NS>(c, gk, i, r0, RN);
     }
 }
 
-cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
-                            cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
+template <int NS>
+cudaError_t launch_pool_csr_t(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                              const GleF32& gk, cudaStream_t st) {
     static const int resident = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_csr_kernel, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pool_csr_kernel<NS>, 256, 0);
         return std::max(1, sms * std::max(per, 1));
     }();
     const int grid = std::min(nitems, resident);
-    pool_csr_kernel<<<grid, 256, 0, st>>>(desc, items, nitems, RN);
+    pool_csr_kernel<NS><<<grid, 256, 0, st>>>(desc, items, nitems, RN, gk);
     return cudaGetLastError();
+}
+
+cudaError_t launch_pool_csr(const PoolDesc* desc, const PoolRowItem* items, int nitems, int RN,
+                            int ns, const GleF32& gk, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    switch (ns) {
+        case 1: return launch_pool_csr_t<1>(desc, items, nitems, RN, gk, st);
+        case 2: return launch_pool_csr_t<2>(desc, items, nitems, RN, gk, st);
+        case 3: return launch_pool_csr_t<3>(desc, items, nitems, RN, gk, st);
+        case 4: return launch_pool_csr_t<4>(desc, items, nitems, RN, gk, st);
+        case 5: return launch_pool_csr_t<5>(desc, items, nitems, RN, gk, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ convergence
