@@ -99,11 +99,20 @@ fth_status admit(fth_server* S, int64_t* admitted) {
             it = S->queue.erase(it);
             continue;
         }
-        if (st != FTH_E_WORKSPACE) {
-            // invalid request: finish it with its status, keep serving the others
+        bool never_fits = false;
+        if (st == FTH_E_WORKSPACE) {
+            // a request larger than the whole slab would block the queue for ever
+            size_t need = 0;
+            fth_pool_stats_t ps;
+            never_fits = fth_pool_footprint(S->pool, &r.M, &r.gle, &r.po, &need) == FTH_OK &&
+                         fth_pool_stats(S->pool, &ps) == FTH_OK && need > ps.slab_bytes;
+        }
+        if (st != FTH_E_WORKSPACE || never_fits) {
+            // invalid (or never admissible) request: finish it, keep serving the others
             r.state = FTH_REQ_FAILED;
             r.t_done = S->now();
-            S->last_error = fth_pool_last_error(S->pool);
+            S->last_error = never_fits ? std::string("request larger than the pool's workspace")
+                                       : std::string(fth_pool_last_error(S->pool));
             it = S->queue.erase(it);
             continue;
         }

@@ -397,3 +397,37 @@ def test_functional_dense_all_elements_tf32_tiles():
         # BF16x3 force: trajectories agree to ~3e-4 of their scale
         assert abs(v - vo) <= 2e-3 * abs(vo)
         assert abs(e - eo) <= 2e-2 * eo
+
+
+def test_trace_of_log_on_paper_m1_lattice():
+    """End to end on the paper's M1 recipe at n = 7: the ln fit on [e, 100e], M1 scaled
+    into it, Tr ln(r M1) from the trace functional, against the oracle's exact expected
+    running mean (within 4 error bars) and through the inverse transform against
+    Tr ln M1 (within the error bar plus the fit's bias)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle import gle
+    from paper_1402_2095_gb300 import FTH, fit, transforms
+    from paper_1402_2095_gb300.binding import trace_terms
+    n1 = 7
+    N = n1 ** 3
+    rowptr, col, val = syn.m1_csr(n1, seed=91)
+    A = sp.csr_matrix((val, col, rowptr), shape=(N, N))
+    lo = float(spla.eigsh(A, k=1, which="SA", return_eigenvectors=False)[0])
+    a_p, c_p, dt, rep = fit.load_gle("log_e_100e")
+    r = float(np.e) * 1.0005 / lo
+    v32 = (r * val).astype(np.float32)
+    g = FTH(csr=(rowptr, col, v32, N), a_p=a_p, c_p=c_p, dt=dt, replicas=64, seed=92,
+            track="diag", block=500)
+    fid = g.add_functional(*trace_terms(n=N))
+    steps = 6000
+    g.run(steps)
+    tr_s, err_s = g.functional(fid)
+    Ms = sp.csr_matrix((v32.astype(np.float64), col, rowptr), shape=(N, N)).toarray()
+    lam = np.linalg.eigvalsh(Ms)
+    T, S = gle.propagator(a_p, c_p, dt)
+    expected = float(np.sum(gle.mode_response_mean(lam, T, S, dt, 0, steps)))
+    assert abs(tr_s - expected) <= 4 * err_s
+    exact_log_trace = float(np.sum(np.log(np.linalg.eigvalsh(A.toarray()))))
+    got = transforms.log_trace_from_scaled(tr_s, N, r)
+    assert abs(got - exact_log_trace) <= 4 * err_s + 2 * rep["max_rel_err"] * abs(tr_s)

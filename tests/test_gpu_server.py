@@ -131,3 +131,22 @@ def test_server_rejects_invalid_and_keeps_serving():
     assert srv.result(ib)[0]["state"] == "failed"
     assert srv.result(ig)[0]["state"] in ("done", "budget")
     srv.close()
+
+
+def test_server_fails_requests_that_can_never_fit():
+    """A request larger than the whole workspace fails instead of blocking the queue."""
+    from paper_1402_2095_gb300 import Server
+    reqs = _requests()
+    big = dict(reqs[1])
+    M, _, _ = syn.dense_spd(2000, 1.0, 100.0, seed=99)
+    big["M"] = M
+    big["pairs"] = np.concatenate([syn.diag_pairs(2000)[:16], syn.random_pairs(2000, 16, seed=1)])
+    srv = Server(24 << 20, replicas=32, max_problems=4, chunk_steps=100, min_blocks=2,
+                 max_bypass=0)
+    ib = srv.submit(**big, target=0.5)
+    ig = srv.submit(**reqs[2], target=0.5, max_steps=300)
+    for _ in range(6):
+        srv.step()
+    assert srv.result(ib)[0]["state"] == "failed"
+    assert srv.result(ig)[0]["state"] in ("done", "budget")
+    srv.close()
