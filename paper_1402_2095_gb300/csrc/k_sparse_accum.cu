@@ -153,20 +153,39 @@ pair_accum_rows_kernel(const float* __restrict__ ps, int64_t ps_ld, const int32_
         const float4* ra = reinterpret_cast<const float4*>(ps + i * ps_ld);
 #pragma unroll
         for (int v = 0; v < V; ++v) a[v] = ra[v * 32 + lane];
-        for (int k = k0; k < k1; ++k) {
-            const float4* rb = reinterpret_cast<const float4*>(ps + (int64_t)pcol[k] * ps_ld);
-            float acc = 0.f;
+        // partners two at a time: both rows' loads are in flight before the FMAs
+        for (int k = k0; k < k1; k += 2) {
+            const bool two = k + 1 < k1;
+            const float4* rb0 = reinterpret_cast<const float4*>(ps + (int64_t)pcol[k] * ps_ld);
+            const float4* rb1 =
+                reinterpret_cast<const float4*>(ps + (int64_t)pcol[two ? k + 1 : k] * ps_ld);
+            float4 b0[V], b1[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float4 b = rb[v * 32 + lane];
-                acc = fmaf(a[v].x, b.x, acc);
-                acc = fmaf(a[v].y, b.y, acc);
-                acc = fmaf(a[v].z, b.z, acc);
-                acc = fmaf(a[v].w, b.w, acc);
+                b0[v] = rb0[v * 32 + lane];
+                b1[v] = rb1[v * 32 + lane];
+            }
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc0 = fmaf(a[v].x, b0[v].x, acc0);
+                acc1 = fmaf(a[v].x, b1[v].x, acc1);
+                acc0 = fmaf(a[v].y, b0[v].y, acc0);
+                acc1 = fmaf(a[v].y, b1[v].y, acc1);
+                acc0 = fmaf(a[v].z, b0[v].z, acc0);
+                acc1 = fmaf(a[v].z, b1[v].z, acc1);
+                acc0 = fmaf(a[v].w, b0[v].w, acc0);
+                acc1 = fmaf(a[v].w, b1[v].w, acc1);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) partial[pe[k]] += acc;
+            for (int o = 16; o > 0; o >>= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            }
+            if (lane == 0) {
+                partial[pe[k]] += acc0;
+                if (two) partial[pe[k + 1]] += acc1;
+            }
         }
     }
 }
