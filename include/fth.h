@@ -16,6 +16,9 @@
  * S lower triangular (a pivot at or below 1e-14 of the largest diagonal entry is an
  * exact zero), xi standard normals from Philox4x32-10 (counter (kappa, i, r, k), key
  * = seed) through Box-Muller.  Samples of p (or q) are taken at the end of each step.
+ * The two O half-steps around a sample (end of step kappa-1, start of step kappa) are
+ * drawn jointly from their exact joint law with s + 2 normals of kappa (same Markov
+ * chain as two independent half-steps); the first step's start half uses s + 1.
  *
  * Conventions shared by every entry point:
  *  - Every call returns an fth_status; none aborts.  After an error,
