@@ -76,7 +76,7 @@ cudaError_t launch_pool_convert(const void* src, int f64, int n, int np, int r0,
 cudaError_t launch_pool_progress(const PoolDesc* desc, const int* live, int nlive, double* out,
                                  cudaStream_t st);
 constexpr size_t kPoolStageBytes = size_t(16) << 20;   // host-to-device staging of M rows
-constexpr int kPoolGleVariants = 3;
+constexpr int kPoolGleVariants = 4;
 cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem* items,
                             int nitems, int RN, int kind, int ns, const GleF32& gk,
                             cudaStream_t st);

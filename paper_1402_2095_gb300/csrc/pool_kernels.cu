@@ -314,6 +314,7 @@ struct PoolGleShared {
 };
 
 template <int NE> struct VecF;
+template <> struct VecF<1> { using T = float; };
 template <> struct VecF<2> { using T = float2; };
 template <> struct VecF<4> { using T = float4; };
 
@@ -457,7 +458,8 @@ cudaError_t launch_pool_gle_ns(int variant, const PoolDesc* desc, const PoolRowI
     switch (variant) {
         case 0: return launch_pool_gle_t<4, 2, NS>(desc, items, nitems, RN, kind, gk, st);
         case 1: return launch_pool_gle_t<2, 3, NS>(desc, items, nitems, RN, kind, gk, st);
-        case 2: return launch_pool_gle_t<4, 3, NS>(desc, items, nitems, RN, kind, gk, st);
+        case 2: return launch_pool_gle_t<1, 4, NS>(desc, items, nitems, RN, kind, gk, st);
+        case 3: return launch_pool_gle_t<1, 6, NS>(desc, items, nitems, RN, kind, gk, st);
         default: return cudaErrorInvalidValue;
     }
 }
