@@ -7,8 +7,10 @@ prints the shift with its sign flipped; affine_map() uses the form derived from
 r lo + m = lo' and r hi + m = hi'.
 
 Inverse transforms: ln M = ln(r M) - I ln r (a fit of ln on a range where it is
-positive serves any M whose scaled spectrum falls inside it), and
-exp(-a M) = exp(-a (M + m I)) e^{a m} (a shift makes an indefinite M positive definite).
+positive serves any M whose scaled spectrum falls inside it),
+exp(-a M) = exp(-a (M + m I)) e^{a m} (a shift makes an indefinite M positive definite),
+and for a power law f(x) = x^k, f(M) = f(r M) r^-k (one fit serves every spectrum that a
+scaling r moves into its range).
 """
 from __future__ import annotations
 
@@ -48,3 +50,8 @@ def log_trace_from_scaled(trace_of_log_rM: float, n: int, r: float) -> float:
 def exp_from_shifted(values, a: float, m: float):
     """Elements (or the trace) of exp(-a M) from those of exp(-a (M + m I))."""
     return np.asarray(values, dtype=np.float64) * np.exp(a * m)
+
+
+def power_from_scaled(values, r: float, k: float):
+    """Elements of M^k from those of (r M)^k."""
+    return np.asarray(values, dtype=np.float64) * float(r) ** (-k)

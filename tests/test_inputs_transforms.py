@@ -70,3 +70,12 @@ def test_affine_map_and_transforms():
     assert np.allclose(tr.exp_from_shifted(Es, A, 200.0), E)     # M - 200 I shifted by m = 200
     ap, cp = tr.scale_gle(np.eye(2), np.eye(2), alpha=2.0, gamma=3.0)
     assert np.allclose(ap, 2 * np.eye(2)) and np.allclose(cp, 3 * np.eye(2))
+
+
+def test_power_law_rescale():
+    g = np.random.default_rng(10)
+    Q, _ = np.linalg.qr(g.standard_normal((5, 5)))
+    M = (Q * np.array([0.6, 1.5, 4.0, 9.0, 14.0])) @ Q.T
+    r = 2.0
+    f = lambda A: sla.fractional_matrix_power(A, -0.5).real
+    assert np.allclose(tr.power_from_scaled(f(r * M), r, -0.5), f(M))
