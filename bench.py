@@ -631,8 +631,8 @@ class Serving:
     seconds.  Each request: 50 % dense SPD (N uniform in [128, 4096], lambda log-uniform
     in [1, 1e2], Haar Q), 50 % periodic lattice L^3 (L uniform in {16..48}, as the 64^3
     workload); f = x^-1/2 or Fermi beta = 2 (mu = median lambda = 10 dense, 7 lattice),
-    50 / 50, each with a fitted GLE (lattice x^-1/2 requests reuse the [1, 100] fit on 2 M
-    by the paper's scaling relation); relative accuracy target t_hi or t_lo, 50 / 50;
+    50 / 50, each with the GLE fitted to its spectrum range; relative accuracy target t_hi
+    or t_lo, 50 / 50;
     32 tracked elements (16 diagonal, 16 off-diagonal: random pairs dense, nearest
     neighbours lattice); R = 32 replicas; its own Philox key.  Matrices are drawn from
     a seeded set of `distinct` dense and lattice matrices generated before the run."""
@@ -646,7 +646,7 @@ class Serving:
         self.rate, self.window, self.t_hi, self.t_lo, self.budget = rate, window, t_hi, t_lo, budget
         self.arrivals = syn.poisson_arrivals(rate, window, seed=self.seed)
         self.fits = {k: fit.load_gle(k) for k in ("inv_sqrt_1_100", "fermi_b2_1_100",
-                                                   "fermi_b2_lattice")}
+                                                   "inv_sqrt_lattice", "fermi_b2_lattice")}
         self.dense, self.lattice = [], []
         for k in range(distinct):
             n = int(g.integers(128, 4097))
@@ -656,7 +656,7 @@ class Serving:
             rowptr, col, val = syn.lattice_csr(L, seed=self.seed * 100 + k)
             self.lattice.append((rowptr, col, val.astype(np.float32), L ** 3, L))
         self.reqs = []
-        post = {}
+        lattice_inv_sqrt = []
         for j in range(len(self.arrivals)):
             dense = bool(g.integers(0, 2))
             k = int(g.integers(0, distinct))
@@ -673,20 +673,14 @@ class Serving:
                 nn = syn.lattice_nn_pairs(L)
                 pairs = np.concatenate([syn.diag_pairs(n)[g.choice(n, 16, replace=False)],
                                         nn[g.choice(len(nn), 16, replace=False)]])
-                if fermi:
-                    fname = "fermi_b2_lattice"
-                    mat = {"csr": (rowptr, col, val, n)}
-                else:
-                    # fit reuse by scaling (paper's scaling relation): the x^-1/2 fit on
-                    # [1, 100] serves the lattice spectrum [0.5, 14.5] moved by r = 2;
-                    # f(M) = f(2 M) 2^(1/2)
-                    fname = "inv_sqrt_1_100"
-                    mat = {"csr": (rowptr, col, (2.0 * val).astype(np.float32), n)}
-                    post[j] = 2.0 ** 0.5
+                fname = "fermi_b2_lattice" if fermi else "inv_sqrt_lattice"
+                mat = {"csr": (rowptr, col, val, n)}
+                if not fermi:
+                    lattice_inv_sqrt.append(j)
             a_p, c_p, dt, _ = self.fits[fname]
             self.reqs.append(dict(mat, a_p=a_p, c_p=c_p, dt=dt, seed=self.seed * 10000 + j,
                                   block=1000, pairs=pairs, target=target, max_steps=budget))
-        self.post = post     # result scale of requests served through a rescaled fit
+        self.lattice_inv_sqrt = lattice_inv_sqrt
         self.label = (f"Poisson {rate:g} req/s over {window:g} s ({len(self.reqs)} requests); 50% "
                       f"dense N~U[128,4096] / 50% lattice L~U{{16..48}}; f in {{x^-1/2, Fermi b=2}}; "
                       f"targets {t_hi:g}/{t_lo:g} (normwise rel. error bar), budget {budget} "
@@ -729,10 +723,10 @@ def run_serving(args, rank, world, local):
     example = None
     for j, rid in enumerate(ids):
         info, v, e = srv.result(rid)
-        if v is not None and j in wl.post and example is None:
-            # a lattice x^-1/2 request served through the rescaled [1, 100] fit
+        if v is not None and example is None and j in wl.lattice_inv_sqrt:
+            # one returned element of a lattice x^-1/2 request
             example = {"request": j, "element": [int(x) for x in wl.reqs[j]["pairs"][0]],
-                       "f_M": float(v[0] * wl.post[j]), "errbar": float(e[0] * wl.post[j])}
+                       "f_M": float(v[0]), "errbar": float(e[0])}
         states[info["state"]] = states.get(info["state"], 0) + 1
         if info["state"] in ("done", "budget"):
             lat.append(info["t_done"] - c0 - wl.arrivals[j])

@@ -79,3 +79,19 @@ def test_power_law_rescale():
     r = 2.0
     f = lambda A: sla.fractional_matrix_power(A, -0.5).real
     assert np.allclose(tr.power_from_scaled(f(r * M), r, -0.5), f(M))
+
+
+def test_time_scaled_gle_samples_the_scaled_spectrum():
+    """A_p -> alpha A_p with dt -> dt / alpha leaves the discrete OU propagator unchanged and
+    multiplies lambda dt^2 by 1 / alpha^2: the GLE then samples f(M / alpha^2).  Checked on
+    the oracle's exact per-mode response of the discrete integrator."""
+    from oracle import gle
+    a_p, c_p = syn.random_gle(4, seed=31, rate=3.0)
+    dt, alpha = 0.02, 2.0 ** -0.5
+    a2, c2 = tr.scale_gle(a_p, c_p, alpha=alpha)
+    T1, S1 = gle.propagator(a_p, c_p, dt)
+    T2, S2 = gle.propagator(a2, c2, dt / alpha)
+    lams = np.array([0.5, 1.3, 3.0, 7.7, 14.5])
+    g2 = gle.mode_response(lams, T2, S2, dt / alpha)
+    g1 = gle.mode_response(lams / alpha ** 2, T1, S1, dt)
+    assert np.allclose(g2, g1, rtol=1e-10, atol=0)
