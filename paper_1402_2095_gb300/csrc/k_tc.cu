@@ -44,42 +44,26 @@ struct TcMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
-// a_blocks > 0: A is the blocked 3-D map with a_blocks K slices per row block, and the
-// producer also asks L2 to prefetch the A slice a_prefetch slices ahead of the one it
-// loads (A streams from DRAM once; the ring alone holds too few bytes in flight to
-// cover DRAM latency at full rate).
+// a_blocks > 0: A is the blocked 3-D map with a_blocks K slices per row block.
 template <int KIND, int BN, int STAGES>
 __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b_row,
                                             int nslices, uint8_t* stages, uint64_t* full,
                                             uint64_t* empty, uint64_t* done, uint32_t tmem,
-                                            uint32_t* err, int slice0 = 0, int a_blocks = 0,
-                                            int a_prefetch = 0) {
+                                            uint32_t* err, int slice0 = 0, int a_blocks = 0) {
     using C = TcCfg<KIND, BN>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
         bool ok = true;
-        const int blk0 = (a_row / 128) * a_blocks + slice0;
-        const bool pf = a_blocks > 0 && a_prefetch > STAGES;
-        if (pf) {
-            for (int kb = STAGES; kb < a_prefetch && kb < nslices; ++kb) {
-                tma_prefetch_3d(&maps.a_hi, 0, 0, blk0 + kb);
-                if (KIND == 2) tma_prefetch_3d(&maps.a_lo, 0, 0, blk0 + kb);
-            }
-        }
         for (int kb = 0; kb < nslices && ok; ++kb) {
             const int st = kb % STAGES;
-            if (pf && kb + a_prefetch < nslices) {
-                tma_prefetch_3d(&maps.a_hi, 0, 0, blk0 + kb + a_prefetch);
-                if (KIND == 2) tma_prefetch_3d(&maps.a_lo, 0, 0, blk0 + kb + a_prefetch);
-            }
             if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
             if (!ok) break;
             uint8_t* base = stages + st * C::kStageBytes;
             mbar_expect_tx(&full[st], C::kStageBytes);
             const int x = (slice0 + kb) * C::kKPerSlice;
-            const int blk = blk0 + kb;
+            const int blk = (a_row / 128) * a_blocks + slice0 + kb;
             if (a_blocks > 0) tma_load_3d(&maps.a_hi, &full[st], base, 0, 0, blk);
             else tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
             tma_load_2d(&maps.b_hi, &full[st], base + C::kABytes, x, b_row);
@@ -182,9 +166,6 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
 }
 
 // ------------------------------------------------------------------ force GEMM
-// L2 prefetch distance of the force's A (= M) slices, in K slices of 128 bytes.
-constexpr int kForcePrefetch = 12;
-
 // grid (Np / 128, ceil(Rp / BN)); MQ[row][col] for row < N, col < Rp.
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
@@ -196,7 +177,7 @@ tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int
     tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
     const int row0 = blockIdx.x * 128, col0 = blockIdx.y * BN;
     tc_mainloop<KIND, BN, STAGES>(maps, row0, col0, nslices, stages, full, empty, done, tmem, err,
-                                  0, nslices, kForcePrefetch);
+                                  0, nslices);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -264,7 +245,7 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
     const int s0 = (nslices_total * kc) / KSPLIT;
     const int s1 = (nslices_total * (kc + 1)) / KSPLIT;
     tc_mainloop<KIND, BN, STAGES>(maps, row0, 0, s1 - s0, stages, full, empty, done, tmem, err,
-                                  s0, nslices_total, kForcePrefetch);
+                                  s0, nslices_total);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
