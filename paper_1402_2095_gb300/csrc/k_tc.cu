@@ -381,6 +381,145 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
     tc_teardown<1, 256>(tmem);
 }
 
+// 256 x 256 output blocks (Iw <= Jw in 256-row units): two 128 x 256 accumulators (all
+// 512 TMEM columns) share each B slice, so a CTA takes 64 KiB of operands per K slice for
+// twice the MMAs of the 128 x 256 form (a third fewer operand bytes per flop) and the
+// upper triangle fits one wave of CTAs.  On the diagonal A and B are the same rows and
+// one load serves both.  Needs an even number of 128-row blocks.
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1)
+tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, int nbt,
+                  int nslices, uint32_t* err) {
+    constexpr int kSlab = 256 * 128;            // one 256-row x 128-byte K slice
+    constexpr int kStage = 2 * kSlab;           // A rows, then B rows
+    constexpr uint32_t kCols = 512;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* stages = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(stages + STAGES * kStage);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = full + 2 * STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2 * STAGES + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+
+    const int nbw = nbt / 2;
+    int t = blockIdx.x, Iw = 0;
+    while (t >= nbw - Iw) {
+        t -= nbw - Iw;
+        ++Iw;
+    }
+    const int Jw = Iw + t;
+    const bool diag = Iw == Jw;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nslices && ok; ++kb) {
+            const int st = kb % STAGES;
+            if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
+            if (!ok) break;
+            uint8_t* base = stages + st * kStage;
+            mbar_expect_tx(&full[st], diag ? kSlab : kStage);
+            tma_load_2d(&maps.b_hi, &full[st], base + kSlab, kb * 32, Jw * 256);
+            if (!diag) tma_load_2d(&maps.b_hi, &full[st], base, kb * 32, Iw * 256);
+            ++issued;
+        }
+        if (!ok || *reinterpret_cast<volatile uint32_t*>(err) != 0) {
+            for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: rows Iw*256 + 0..127 into columns 0..255, rows + 128..255 into
+        // columns 256..511
+        constexpr uint32_t idesc = make_idesc(2, 256);
+        bool ok = true;
+        for (int kb = 0; kb < nslices; ++kb) {
+            const int st = kb % STAGES;
+            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err)) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t base = smem_u32(stages + st * kStage);
+            const uint32_t abase = diag ? base + kSlab : base;
+            const uint64_t a0 = sw128_desc(abase);
+            const uint64_t a1 = sw128_desc(abase + 128 * 128);
+            const uint64_t b = sw128_desc(base + kSlab);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                umma<1>(tmem, a0 + adv, b + adv, idesc, acc);
+                umma<1>(tmem + 256, a1 + adv, b + adv, idesc, acc);
+            }
+            umma_commit(&empty[st]);
+        }
+        umma_commit(done);
+        if (!ok) atomicOr(err, kErrTimeout);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    if (ok) {
+#pragma unroll 1
+        for (int a = 0; a < 2; ++a) {
+            const int I = 2 * Iw + a;
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                const int J = 2 * Jw + half;
+                if (J < I || J >= nbt || I >= nbt) continue;
+                const int64_t tile = (int64_t)I * nbt - ((int64_t)I * (I - 1)) / 2 + (J - I);
+                float* out = tiles + tile * 128 * 128 + (int64_t)(warp * 32 + lane) * 128;
+#pragma unroll 1
+                for (int c = 0; c < 8; ++c) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) +
+                                  (uint32_t)(a * 256 + half * 128 + c * 16),
+                              v);
+                    float4* dst = reinterpret_cast<float4*>(out + c * 16);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float4 o = dst[j];
+                        o.x += v[4 * j];
+                        o.y += v[4 * j + 1];
+                        o.z += v[4 * j + 2];
+                        o.w += v[4 * j + 3];
+                        dst[j] = o;
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kCols));
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -433,6 +572,7 @@ constexpr int kForceBN = 64;
 constexpr int kForceStages = 6;
 constexpr int kSyrkStages = 6;
 constexpr int kSyrkWideStages = 4;
+constexpr int kSyrkSqStages = 3;
 constexpr int kWideBN = 256;
 constexpr int kKSplit = 4;
 
@@ -574,6 +714,15 @@ cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t*
     if (ncols <= 0) return cudaSuccess;
     const int nbt = (int)(ts->Np / 128);
     const int nslices = (int)((ncols + 31) / 32);
+    if (nbt >= 2 && nbt % 2 == 0) {
+        const int nbw = nbt / 2;
+        const unsigned nctas = (unsigned)(nbw * (nbw + 1) / 2);
+        const size_t sm = (size_t)kSyrkSqStages * 2 * 256 * 128 + 1024 + 8 * (2 * kSyrkSqStages + 2);
+        auto kern = tc_syrk_sq_kernel<kSyrkSqStages>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<nctas, 128, sm, st>>>(ts->maps_wide, tiles, nbt, nslices, err);
+        return cudaGetLastError();
+    }
     if (ts->Np >= 256) {
         const int nbw = (nbt + 1) / 2;
         unsigned nctas = 0;

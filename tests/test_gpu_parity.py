@@ -131,12 +131,15 @@ def test_accumulation_parity_fp64_all():
     assert np.allclose(errs_g, errs_o, rtol=1e-8, atol=1e-14)
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16x3", "fp32"])
-def test_all_elements_one_sample(precision):
+@pytest.mark.parametrize("precision,n", [("tf32", 300), ("bf16x3", 300), ("fp32", 300),
+                                         ("tf32", 500), ("bf16x3", 500)])
+def test_all_elements_one_sample(precision, n):
     # A_p = C_p = 0, p0 = 0, observable q: the single sample of run(1) is
     # q1 = q0 - (dt^2/2) M q0 exactly, so <q1 q1^T> is known for every element.
+    # n = 300: three 128-row blocks (128 x 256 accumulator tiles); n = 500: four blocks,
+    # 256 x 256 tiles on and off the diagonal, padded rows at the end.
     from paper_1402_2095_gb300 import FTH
-    n, R, dt = 300, 64, 0.01
+    R, dt = 64, 0.01
     M = _dense(n, seed=31).astype(np.float32).astype(np.float64)
     q0 = syn.gaussian_state((R, n), seed=32)
     z = np.zeros((5, 5))
