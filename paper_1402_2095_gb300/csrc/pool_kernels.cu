@@ -486,7 +486,9 @@ cudaError_t launch_pool_gle(int variant, const PoolDesc* desc, const PoolRowItem
 // Warp tasks as in the dense step: 4 rows x 32 replicas per pass, 8 lanes per row with 4
 // replicas each, so the state rows and every neighbour row q[j][r0 .. r0+3] a row's
 // lanes gather are whole 128-byte segments; the row's column indices and values are
-// broadcast loads.  Positions ping-pong between q[cur] and q[cur ^ 1].
+// broadcast loads.  Positions ping-pong between q[cur] and q[cur ^ 1].  Three blocks per
+// SM (80 registers, a few spilled) beat two (116 registers) by 8 % on a serving mix of
+// lattices: the gathers need the extra warps in flight.
 struct PoolCsrShared {
     uint32_t rk[20];
     uint32_t roff;
@@ -545,7 +547,7 @@ __device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, const GleF
 }
 
 template <int NS>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 pool_csr_kernel(const PoolDesc* __restrict__ desc, const PoolRowItem* __restrict__ items,
                 int nitems, int RN, const GleF32 gk) {
     __shared__ PoolCsrShared cs[8];
