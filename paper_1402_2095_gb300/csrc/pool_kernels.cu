@@ -10,8 +10,9 @@
 //                       bulk copies land them in the SWIZZLE_128B layout the MMA reads;
 //   pool_gle_kernel     dense problems: the element-wise fused GLE step;
 //   pool_csr_kernel     CSR problems: fused SpMM + GLE step;
-//   pool_accum_kernel   one CTA per live problem: accumulate its tracked pairs for this
-//                       sample, advance its counters and flush its own completed blocks.
+//   pool_accum_kernel   items of up to 256 tracked pairs: accumulate this sample; the
+//                       last item of a problem advances its counters and flushes its
+//                       completed blocks.
 // A problem's first launch is its prologue (start half only), exactly as a standalone
 // context; its noise (key = its seed) and arithmetic order do not depend on the other
 // problems in the pool, so its results are identical alone and in any mix.
@@ -715,9 +716,11 @@ cudaError_t launch_pool_convert(const void* src, int f64, int n, int np, int r0,
 }
 
 // ------------------------------------------------------------------ accumulate, advance, flush
-// Items of up to kPoolAccChunk tracked pairs, one thread per pair: the thread sums
-// x_i^r x_j^r over the replicas (two contiguous rows of the sample) and adds it to the
-// pair's block partial.  The last item of a problem to finish (a counter in its
+// Items of up to kPoolAccChunk tracked pairs.  RN / 4 lanes share a pair: each loads one
+// 16-byte vector of the two sample rows, so a warp's loads are whole rows (coalesced)
+// rather than 32 scattered rows; the group's dot products are summed by shuffles and
+// added to the pair's block partial.  Four passes of the block have their loads in
+// flight together.  The last item of a problem to finish (a counter in its
 // descriptor, after a fence) advances the problem's counters and, at a block end,
 // folds the block means into the FP64 Welford sums.  A prologue launch only marks the
 // problem primed.
@@ -731,33 +734,36 @@ pool_accum_kernel(PoolDesc* __restrict__ desc, const PoolAccItem* __restrict__ i
         const PoolAccItem it = items[j];
         PoolDesc& d = desc[it.problem];
         const bool take = d.primed && d.nsamp >= d.burnin;
-        const int e = it.e0 + (int)threadIdx.x;
-        if (take && e < it.e1) {
-            const float4* a = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e] * RN);
-            const float4* b = reinterpret_cast<const float4*>(d.x + (size_t)d.pairs[2 * e + 1] * RN);
-            float acc0 = 0.f, acc1 = 0.f;
-            // rows of 32 replicas: all 16 loads of a chunk in flight before the FMAs
+        if (take) {
+            constexpr int kLanes = RN / 4;          // lanes per pair
+            constexpr int kGroups = 256 / kLanes;   // pairs per pass
+            constexpr int kBatch = 4;               // passes with loads in flight together
+            const int sub = (int)threadIdx.x % kLanes, grp = (int)threadIdx.x / kLanes;
+            for (int base = it.e0; base < it.e1; base += kBatch * kGroups) {
+                int ea[kBatch];
+                float4 u[kBatch], v[kBatch];
 #pragma unroll
-            for (int r0 = 0; r0 < RN / 4; r0 += 8) {
-                float4 u[8], v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    u[k] = a[r0 + k];
-                    v[k] = b[r0 + k];
+                for (int k = 0; k < kBatch; ++k) {
+                    ea[k] = base + k * kGroups + grp;
+                    u[k] = v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ea[k] < it.e1) {
+                        const int ia = d.pairs[2 * ea[k]], ib = d.pairs[2 * ea[k] + 1];
+                        u[k] = reinterpret_cast<const float4*>(d.x + (size_t)ia * RN)[sub];
+                        v[k] = reinterpret_cast<const float4*>(d.x + (size_t)ib * RN)[sub];
+                    }
                 }
 #pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    acc0 = fmaf(u[k].x, v[k].x, acc0);
-                    acc1 = fmaf(u[k + 1].x, v[k + 1].x, acc1);
-                    acc0 = fmaf(u[k].y, v[k].y, acc0);
-                    acc1 = fmaf(u[k + 1].y, v[k + 1].y, acc1);
-                    acc0 = fmaf(u[k].z, v[k].z, acc0);
-                    acc1 = fmaf(u[k + 1].z, v[k + 1].z, acc1);
-                    acc0 = fmaf(u[k].w, v[k].w, acc0);
-                    acc1 = fmaf(u[k + 1].w, v[k + 1].w, acc1);
+                for (int k = 0; k < kBatch; ++k) {
+                    float acc = u[k].x * v[k].x;
+                    acc = fmaf(u[k].y, v[k].y, acc);
+                    acc = fmaf(u[k].z, v[k].z, acc);
+                    acc = fmaf(u[k].w, v[k].w, acc);
+#pragma unroll
+                    for (int o = kLanes / 2; o > 0; o >>= 1)
+                        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (sub == 0 && ea[k] < it.e1) d.partial[ea[k]] += acc;
                 }
             }
-            d.partial[e] += acc0 + acc1;
         }
         // the barrier orders every thread's partial store before thread 0's gpu-scope
         // fence, which releases them all before the completion count (the pattern of a
