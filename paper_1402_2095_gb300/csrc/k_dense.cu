@@ -28,6 +28,12 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, i
                  uint32_t kappa, int flags, int observable, float* __restrict__ ps,
                  int64_t ps_ld, int64_t slot_off, int op_kind, void* op_hi, void* op_lo,
                  int Np) {
+    // programmatic dependent launch both ways: this grid may be resident before the force
+    // GEMM it follows has finished, so it waits for it before touching memory; then it
+    // lets the next force GEMM start its setup on SMs it leaves free (that kernel waits
+    // for this grid before reading q)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
     if (i >= N || r0 >= Rp) return;
@@ -94,15 +100,24 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
                              cudaStream_t st) {
-    dim3 block(32, 8);
-    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((Rp / 4 + 7) / 8));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((N + 31) / 32), (unsigned)((Rp / 4 + 7) / 8));
+    cfg.blockDim = dim3(32, 8);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     const int64_t slot_off = slot * Rp;
 #define FTH_DENSE_CASE(NSV)                                                                   \
-    case NSV:                                                                                 \
-        dense_gle_kernel<NSV><<<grid, block, 0, st>>>(                                        \
-            g, (int)N, (int)R, (int)Rp, MQ, mq_planes, q, p, s, kappa, flags, observable,     \
-            ps, ps_ld, slot_off, op_kind, op_hi, op_lo, (int)Np);                             \
-        break;
+    case NSV: {                                                                               \
+        const cudaError_t e = cudaLaunchKernelEx(                                             \
+            &cfg, dense_gle_kernel<NSV>, g, (int)N, (int)R, (int)Rp, MQ, mq_planes, q, p, s,  \
+            kappa, flags, observable, ps, ps_ld, slot_off, op_kind, op_hi, op_lo, (int)Np);   \
+        if (e != cudaSuccess) return e;                                                       \
+        break;                                                                                \
+    }
     switch (ns) {
         FTH_DENSE_CASE(1)
         FTH_DENSE_CASE(2)

@@ -49,29 +49,51 @@ template <int KIND, int BN, int STAGES>
 __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b_row,
                                             int nslices, uint8_t* stages, uint64_t* full,
                                             uint64_t* empty, uint64_t* done, uint32_t tmem,
-                                            uint32_t* err, int slice0 = 0, int a_blocks = 0) {
+                                            uint32_t* err, int slice0 = 0, int a_blocks = 0,
+                                            bool dep_wait = false) {
     using C = TcCfg<KIND, BN>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer.  With dep_wait (a programmatic dependent launch whose B operand
+        // is written by the previous kernel) the A slices of the first ring fill, which
+        // no earlier kernel writes, are issued before the grid dependency wait.
         int issued = 0;
         bool ok = true;
+        const int early = dep_wait ? std::min(STAGES, nslices) : 0;
+        for (int kb = 0; kb < early; ++kb) {
+            uint8_t* base = stages + kb * C::kStageBytes;
+            mbar_expect_tx(&full[kb], C::kStageBytes);
+            const int x = (slice0 + kb) * C::kKPerSlice;
+            const int blk = (a_row / 128) * a_blocks + slice0 + kb;
+            if (a_blocks > 0) tma_load_3d(&maps.a_hi, &full[kb], base, 0, 0, blk);
+            else tma_load_2d(&maps.a_hi, &full[kb], base, x, a_row);
+            if (KIND == 2) {
+                if (a_blocks > 0) tma_load_3d(&maps.a_lo, &full[kb], base + C::kABytes + C::kBBytes, 0, 0, blk);
+                else tma_load_2d(&maps.a_lo, &full[kb], base + C::kABytes + C::kBBytes, x, a_row);
+            }
+        }
+        if (dep_wait) {
+            grid_dependency_wait();
+            allow_dependent_launch();
+        }
         for (int kb = 0; kb < nslices && ok; ++kb) {
             const int st = kb % STAGES;
             if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
             if (!ok) break;
             uint8_t* base = stages + st * C::kStageBytes;
-            mbar_expect_tx(&full[st], C::kStageBytes);
             const int x = (slice0 + kb) * C::kKPerSlice;
-            const int blk = (a_row / 128) * a_blocks + slice0 + kb;
-            if (a_blocks > 0) tma_load_3d(&maps.a_hi, &full[st], base, 0, 0, blk);
-            else tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
-            tma_load_2d(&maps.b_hi, &full[st], base + C::kABytes, x, b_row);
-            if (KIND == 2) {
-                if (a_blocks > 0) tma_load_3d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, 0, 0, blk);
-                else tma_load_2d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, x, a_row);
-                tma_load_2d(&maps.b_lo, &full[st], base + 2 * C::kABytes + C::kBBytes, x, b_row);
+            if (kb >= early) {
+                mbar_expect_tx(&full[st], C::kStageBytes);
+                const int blk = (a_row / 128) * a_blocks + slice0 + kb;
+                if (a_blocks > 0) tma_load_3d(&maps.a_hi, &full[st], base, 0, 0, blk);
+                else tma_load_2d(&maps.a_hi, &full[st], base, x, a_row);
+                if (KIND == 2) {
+                    if (a_blocks > 0) tma_load_3d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, 0, 0, blk);
+                    else tma_load_2d(&maps.a_lo, &full[st], base + C::kABytes + C::kBBytes, x, a_row);
+                }
             }
+            tma_load_2d(&maps.b_hi, &full[st], base + C::kABytes, x, b_row);
+            if (KIND == 2) tma_load_2d(&maps.b_lo, &full[st], base + 2 * C::kABytes + C::kBBytes, x, b_row);
             ++issued;
         }
         if (!ok || *reinterpret_cast<volatile uint32_t*>(err) != 0) {
@@ -240,12 +262,18 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
     uint64_t *full, *empty, *done;
     uint32_t tmem;
     tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
+    // programmatic dependent launch: setup above overlaps the previous kernel's tail;
+    // q^T and MQ are touched only after the wait (the producer waits inside the mainloop)
+    if (threadIdx.x != 0) {
+        grid_dependency_wait();
+        allow_dependent_launch();   // the element-wise kernel waits for this grid's end
+    }
     const int row0 = blockIdx.x * 128;
     const int kc = (int)cluster_rank();
     const int s0 = (nslices_total * kc) / KSPLIT;
     const int s1 = (nslices_total * (kc + 1)) / KSPLIT;
     tc_mainloop<KIND, BN, STAGES>(maps, row0, 0, s1 - s0, stages, full, empty, done, tmem, err,
-                                  s0, nslices_total);
+                                  s0, nslices_total, true);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -643,13 +671,15 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
     cfg.blockDim = dim3(128, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = kKSplit;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const int nslices = (int)(KIND == 1 ? tf->Np / 32 : tf->Np / 64);
     return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
                               nslices, err);
