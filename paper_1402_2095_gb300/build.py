@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfth.so")
 SOURCES = ["fth_host.cu", "k_dense.cu", "k_sparse_accum.cu", "k_fp64.cu", "k_tc.cu", "noalloc.cu",
-           "pool.cu", "pool_kernels.cu", "server.cu"]
+           "pool.cu", "pool_kernels.cu", "server.cu", "k_prepare.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

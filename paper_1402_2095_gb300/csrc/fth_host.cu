@@ -939,66 +939,48 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
         FTH_CK_C(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
     }
 
-    // ---- M: bring to host FP64 (validation, conversion), then upload
+    // ---- M: dense matrices are validated and converted on the device (k_prepare.cu), from
+    // the caller's device buffer directly or, for a host matrix, in chunks of rows staged
+    // through the part of the workspace after M (zeroed again afterwards); sparse ones on
+    // the host, where their structure is checked
     const int64_t N = L.N;
     const size_t esz_in = Min->dtype == FTH_F64 ? 8 : 4;
     if (Min->kind == FTH_DENSE) {
-        std::vector<double> m((size_t)N * N);
-        {
-            std::vector<uint8_t> raw((size_t)N * N * esz_in);
-            if (Min->on_device) {
-                FTH_CK_C(cudaMemcpy(raw.data(), Min->values, raw.size(), cudaMemcpyDeviceToHost), "d2h M");
-            } else {
-                std::memcpy(raw.data(), Min->values, raw.size());
-            }
-            for (size_t k = 0; k < m.size(); ++k)
-                m[k] = esz_in == 8 ? reinterpret_cast<const double*>(raw.data())[k]
-                                   : (double)reinterpret_cast<const float*>(raw.data())[k];
-        }
-        for (int64_t i = 0; i < N; ++i) {
-            if (!(m[i * N + i] > 0.0)) {
-                c->last_error = "M has a non-positive diagonal entry: not positive definite";
-                return bail(FTH_E_NOT_SPD);
-            }
-        }
-        for (double x : m)
-            if (!std::isfinite(x)) {
-                c->last_error = "M has non-finite entries";
-                return bail(FTH_E_INVALID_ARG);
-            }
-        const int64_t Np = L.Np;
-        if (L.path == kPathDense64) {
-            std::vector<double> h((size_t)N * Np, 0.0);
-            for (int64_t i = 0; i < N; ++i)
-                for (int64_t j = 0; j < N; ++j) h[i * Np + j] = m[i * N + j];
-            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream), "h2d M");
-            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
-        } else if (L.precision == FTH_PREC_BF16X3) {
-            // blocked [Np/128][Np/64][128][64]: each tensor-memory A box is contiguous
-            std::vector<uint16_t> h((size_t)Np * Np, 0), l((size_t)Np * Np, 0);
-            for (int64_t i = 0; i < N; ++i)
-                for (int64_t j = 0; j < N; ++j) {
-                    const float x = (float)m[i * N + j];
-                    const uint16_t hb = bf16_rne(x);
-                    const size_t at = blocked_index(i, j, Np, 64);
-                    h[at] = hb;
-                    l[at] = bf16_rne(x - bf16_to_f(hb));
-                }
-            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M hi");
-            FTH_CK_C(cudaMemcpyAsync(c->Mlo, l.data(), l.size() * 2, cudaMemcpyHostToDevice, c->stream), "h2d M lo");
-            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        const int layout = L.path == kPathDense64            ? kPrepF64
+                           : L.precision == FTH_PREC_BF16X3  ? kPrepBf16x3
+                           : L.precision == FTH_PREC_TF32    ? kPrepTf32
+                                                             : kPrepF32;
+        const int f64 = esz_in == 8 ? 1 : 0;
+        if (Min->on_device) {
+            FTH_CK_C(launch_dense_prepare(Min->values, f64, N, 0, N, L.Np, layout, c->M, c->Mlo, c->err,
+                                          c->stream),
+                     "prepare M");
         } else {
-            // FP32 path: row-major [Np][Np]; TF32 path: blocked [Np/128][Np/32][128][32]
-            std::vector<float> h((size_t)Np * Np, 0.f);
-            const bool tf = L.precision == FTH_PREC_TF32;
-            for (int64_t i = 0; i < N; ++i)
-                for (int64_t j = 0; j < N; ++j) {
-                    const float x = (float)m[i * N + j];
-                    if (tf) h[blocked_index(i, j, Np, 32)] = tf32_rna(x);
-                    else h[i * Np + j] = x;
-                }
-            FTH_CK_C(cudaMemcpyAsync(c->M, h.data(), h.size() * 4, cudaMemcpyHostToDevice, c->stream), "h2d M");
-            FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+            uint8_t* stage = c->ws + L.off_q0;
+            const size_t span = L.total - L.off_q0;
+            const size_t row_bytes = (size_t)N * esz_in;
+            const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)(span / row_bytes)));
+            for (int64_t r0 = 0; r0 < N; r0 += rows) {
+                const int64_t nr = std::min<int64_t>(rows, N - r0);
+                FTH_CK_C(cudaMemcpyAsync(stage, static_cast<const uint8_t*>(Min->values) + (size_t)r0 * row_bytes,
+                                         (size_t)nr * row_bytes, cudaMemcpyHostToDevice, c->stream),
+                         "h2d M");
+                FTH_CK_C(launch_dense_prepare(stage, f64, N, r0, nr, L.Np, layout, c->M, c->Mlo, c->err,
+                                              c->stream),
+                         "prepare M");
+            }
+        }
+        uint32_t flags = 0;
+        FTH_CK_C(cudaMemcpyAsync(&flags, c->err, 4, cudaMemcpyDeviceToHost, c->stream), "d2h flags");
+        FTH_CK_C(cudaMemsetAsync(c->ws + L.off_q0, 0, L.total - L.off_q0, c->stream), "zero workspace");
+        FTH_CK_C(cudaStreamSynchronize(c->stream), "sync");
+        if (flags & kPrepNotSpd) {
+            c->last_error = "M has a non-positive diagonal entry: not positive definite";
+            return bail(FTH_E_NOT_SPD);
+        }
+        if (flags & kPrepNonFinite) {
+            c->last_error = "M has non-finite entries";
+            return bail(FTH_E_INVALID_ARG);
         }
     } else {
         const int64_t nnz = L.nnz;

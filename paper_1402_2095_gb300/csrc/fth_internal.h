@@ -56,6 +56,16 @@ void fill_gle_constants(int ns, const double* T, const double* S, GleF32* g32, G
 // Bits of the device error word.
 enum : uint32_t { kErrTimeout = 1u, kErrNonFinite = 2u };
 
+// Dense M preparation on the device (k_prepare.cu): target layouts and validation flags.
+enum : int { kPrepF64 = 0, kPrepF32 = 1, kPrepTf32 = 2, kPrepBf16x3 = 3 };
+enum : uint32_t { kPrepNotSpd = 1u, kPrepNonFinite = 2u };
+// Rows r0 .. r0 + nr - 1 of a row-major n x n matrix at src (device memory holding just
+// those rows; FP64 if f64, else FP32) into the layout's buffer(s) hi (and lo for BF16x3)
+// of order Np; atomically ORs kPrepNotSpd / kPrepNonFinite into *flags.
+cudaError_t launch_dense_prepare(const void* src, int f64, int64_t n, int64_t r0, int64_t nr,
+                                 int64_t Np, int layout, void* hi, void* lo, uint32_t* flags,
+                                 cudaStream_t st);
+
 // Flags of the dense element-wise GLE kernel.
 enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4 };
 
