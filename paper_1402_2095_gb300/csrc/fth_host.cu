@@ -27,7 +27,7 @@ namespace {
 
 thread_local std::string g_thread_error;
 
-constexpr int64_t kGatherChunk = 65536;
+constexpr int64_t kGatherMax = int64_t(1) << 20;   // elements per fth_elements gather pass
 
 int64_t round_up(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -40,7 +40,7 @@ struct Layout {
     Path path;
     int ns;
     int precision, track;
-    int64_t N, R, Rp, Np, nnz, stack, ps_ld, ntracked, count, nbt;
+    int64_t N, R, Rp, Np, nnz, stack, ps_ld, ntracked, count, nbt, gcap;
     size_t off_M = 0, off_Mlo = 0, off_rowptr = 0, off_col = 0, off_val = 0;
     size_t off_q0 = 0, off_q1 = 0, off_p = 0, off_s = 0, off_MQ = 0, off_ophi = 0, off_oplo = 0;
     size_t off_ps = 0, off_ps1 = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
@@ -343,8 +343,11 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
     else L->off_partial = c.take((size_t)std::max<int64_t>(L->count, 1) * 4);
     L->off_mean = c.take((size_t)std::max<int64_t>(L->count, 1) * 8);
     L->off_m2 = c.take((size_t)std::max<int64_t>(L->count, 1) * 8);
-    L->off_gidx = c.take((size_t)kGatherChunk * 8);
-    L->off_gout = c.take((size_t)kGatherChunk * 3 * 8);
+    // gather capacity: every element a request can name (tile-packed count when all are
+    // tracked on the dense FP32 path, where ntracked is 0), at most kGatherMax per pass
+    L->gcap = std::max<int64_t>(1, std::min<int64_t>(std::max(L->ntracked, L->count), kGatherMax));
+    L->off_gidx = c.take((size_t)L->gcap * 8);
+    L->off_gout = c.take((size_t)L->gcap * 3 * 8);
     L->off_err = c.take(256);
     L->total = c.off;
     return FTH_OK;
@@ -424,7 +427,8 @@ struct fth_ctx {
     TcSyrk* tcs = nullptr;
     TcSyrk* tcs1 = nullptr;
     // host-side bookkeeping
-    std::unordered_map<uint64_t, int64_t> pair_index;
+    std::vector<int32_t> reg_pairs;                        // registered pairs (i <= j), in order
+    std::unordered_map<uint64_t, int64_t> pair_index;      // built on the first out-of-order lookup
     int32_t* prow = nullptr;   // tracked pairs grouped by first index (device)
     int32_t* pcol = nullptr;
     int32_t* pe = nullptr;
@@ -1037,12 +1041,10 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
 
     // ---- tracked pairs
     {
-        std::vector<int32_t> pr;
+        std::vector<int32_t>& pr = c->reg_pairs;
         pr.reserve((size_t)L.ntracked * 2);
         auto add = [&](int64_t i, int64_t j) {
             if (i > j) std::swap(i, j);
-            const int64_t idx = (int64_t)pr.size() / 2;
-            c->pair_index.emplace(pair_key(i, j), idx);
             pr.push_back((int32_t)i);
             pr.push_back((int32_t)j);
         };
@@ -1128,8 +1130,11 @@ fth_status fth_status_poll(fth_ctx* c) {
     return FTH_OK;
 }
 
-// Accumulator index of element (i, j), or a NOT_TRACKED / INVALID_ARG status.
-static fth_status element_index(fth_ctx* c, int64_t i, int64_t j, int64_t* out) {
+// Accumulator index of element (i, j), or a NOT_TRACKED / INVALID_ARG status.  `hint` is
+// the position the caller expects (a request in registration order resolves without the
+// map; the map is built on the first lookup that needs it).
+static fth_status element_index(fth_ctx* c, int64_t i, int64_t j, int64_t* out,
+                                int64_t hint = -1) {
     const Layout& L = c->L;
     if (i < 0 || j < 0 || i >= L.N || j >= L.N) {
         c->last_error = "pair index out of range";
@@ -1138,6 +1143,17 @@ static fth_status element_index(fth_ctx* c, int64_t i, int64_t j, int64_t* out) 
     if (L.track == FTH_TRACK_ALL && L.path == kPathDense32) {
         *out = packed_index(i, j, L.nbt);
         return FTH_OK;
+    }
+    const int64_t a = std::min(i, j), b = std::max(i, j);
+    const std::vector<int32_t>& rp = c->reg_pairs;
+    if (hint >= 0 && 2 * hint + 1 < (int64_t)rp.size() && rp[2 * hint] == a && rp[2 * hint + 1] == b) {
+        *out = hint;
+        return FTH_OK;
+    }
+    if (c->pair_index.empty() && !rp.empty()) {
+        c->pair_index.reserve(rp.size() / 2);
+        for (int64_t e = 0; 2 * e < (int64_t)rp.size(); ++e)
+            c->pair_index.emplace(pair_key(rp[2 * e], rp[2 * e + 1]), e);
     }
     auto it = c->pair_index.find(pair_key(i, j));
     if (it == c->pair_index.end()) {
@@ -1166,7 +1182,7 @@ fth_status fth_functional_add(fth_ctx* c, const int64_t* pairs, const double* we
     }
     std::vector<int64_t> idx((size_t)nterms);
     for (int64_t k = 0; k < nterms; ++k) {
-        const fth_status st = element_index(c, pairs[2 * k], pairs[2 * k + 1], &idx[k]);
+        const fth_status st = element_index(c, pairs[2 * k], pairs[2 * k + 1], &idx[k], k);
         if (st != FTH_OK) return st;
         if (!std::isfinite(weights[k])) {
             c->last_error = "non-finite functional weight";
@@ -1227,14 +1243,14 @@ fth_status fth_elements(fth_ctx* c, const int64_t* pairs, int64_t k, double* val
     const Layout& L = c->L;
     std::vector<int64_t> idx((size_t)k);
     for (int64_t e = 0; e < k; ++e) {
-        st = element_index(c, pairs[2 * e], pairs[2 * e + 1], &idx[e]);
+        st = element_index(c, pairs[2 * e], pairs[2 * e + 1], &idx[e], e);
         if (st != FTH_OK) return st;
     }
     const double nb = (double)c->nblocks;
     const double nacc = (double)(c->nblocks * c->block + c->inblock);
-    std::vector<double> out((size_t)kGatherChunk * 3);
-    for (int64_t b0 = 0; b0 < k; b0 += kGatherChunk) {
-        const int64_t m = std::min(kGatherChunk, k - b0);
+    std::vector<double> out((size_t)std::min(L.gcap, std::max<int64_t>(k, 1)) * 3);
+    for (int64_t b0 = 0; b0 < k; b0 += L.gcap) {
+        const int64_t m = std::min(L.gcap, k - b0);
         FTH_CK(cudaMemcpyAsync(c->gidx, idx.data() + b0, m * 8, cudaMemcpyHostToDevice, c->stream),
                "h2d idx");
         const bool p64 = L.path == kPathDense64;
