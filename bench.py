@@ -559,17 +559,20 @@ def run_ragged(args, rank, world, local):
     del pool
     torch.cuda.synchronize()
 
-    # end to end through the public API: host matrices in, every problem's elements out
+    # end to end through the public API: host matrices (pinned) in, every problem's elements out
+    pinned = [torch.from_numpy(m).pin_memory() for m in wl.mats]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = Pool(ws, replicas=wl.R, precision="bf16x3", max_problems=wl.count,
              graph_steps=wl.graph_steps)
-    hs = [g.add(**wl.problem(k, seed_shift=1), replica_offset=rank * wl.R)
+    hs = [g.add(**dict(wl.problem(k, seed_shift=1), M=pinned[k]), replica_offset=rank * wl.R)
           for k in range(wl.count)]
     g.run(steps)
     for k, h in enumerate(hs):
         g.elements(h, wl.pairs[k])
     t_e2e = time.perf_counter() - t0
     g.close()
+    del pinned
     h2d = sum(m.nbytes for m in wl.mats) + sum(p.nbytes for p in wl.pairs)
     d2h = sum(len(p) * 3 * 8 for p in wl.pairs)
 

@@ -974,6 +974,8 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
                          "prepare M");
             }
         }
+        // the context's error word carries the flags here: no other kernel has run yet, and
+        // the zeroing below clears it with the staging span
         uint32_t flags = 0;
         FTH_CK_C(cudaMemcpyAsync(&flags, c->err, 4, cudaMemcpyDeviceToHost, c->stream), "d2h flags");
         FTH_CK_C(cudaMemsetAsync(c->ws + L.off_q0, 0, L.total - L.off_q0, c->stream), "zero workspace");
