@@ -18,9 +18,10 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // -------------------------------------------------------------- element-wise step
-// Thread (i, 4 consecutive replicas); blockDim (32, 8): lanes run along i so the
-// transposed operand stores (q^T[r][i]) are coalesced, and every thread moves one
-// 16-byte vector per plane.
+// Block = 32 rows x 32 replicas: warp w takes rows i0 + 4w .. + 3, eight lanes per row with
+// four consecutive replicas each, so every state-plane access of a warp is four whole
+// 128-byte row segments.  The new positions go through shared memory so the force
+// operand q^T[r][i] is written as 128-byte runs of i (one replica per warp row).
 template <int NS>
 __global__ void __launch_bounds__(256, 4)
 dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, int mq_planes,
@@ -34,62 +35,76 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, i
     // for this grid before reading q)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int r0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
-    if (i >= N || r0 >= Rp) return;
-    const int64_t plane = (int64_t)Np * Rp;
-    const int64_t off = (int64_t)i * Rp + r0;
+    __shared__ float tq[32][33];                 // [replica][row] of the block's tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * 32, rp = blockIdx.y * 32;
+    const int k = warp * 4 + (lane >> 3);        // row within the tile
+    const int i = i0 + k;
+    const int c0 = (lane & 7) * 4;               // first replica within the tile
+    const int r0 = rp + c0;
+    float qn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < N && r0 < Rp) {
+        const int64_t plane = (int64_t)Np * Rp;
+        const int64_t off = (int64_t)i * Rp + r0;
+        // the force may arrive as partial sums over K (one plane per K share)
+        float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
+        for (int pl = 1; pl < mq_planes; ++pl) {
+            const float4 x = *reinterpret_cast<const float4*>(MQ + pl * plane + off);
+            mq4.x += x.x;
+            mq4.y += x.y;
+            mq4.z += x.z;
+            mq4.w += x.w;
+        }
+        float4 q4 = *reinterpret_cast<const float4*>(q + off);
+        float4 v4[NS];
+        v4[0] = *reinterpret_cast<const float4*>(p + off);
+#pragma unroll
+        for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
 
-    // the force may arrive as partial sums over K (one plane per K share)
-    float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
-    for (int pl = 1; pl < mq_planes; ++pl) {
-        const float4 x = *reinterpret_cast<const float4*>(MQ + pl * plane + off);
-        mq4.x += x.x;
-        mq4.y += x.y;
-        mq4.z += x.z;
-        mq4.w += x.w;
-    }
-    float4 q4 = *reinterpret_cast<const float4*>(q + off);
-    float4 v4[NS];
-    v4[0] = *reinterpret_cast<const float4*>(p + off);
-#pragma unroll
-    for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
-
-    float* qa = reinterpret_cast<float*>(&q4);
-    const float* mqa = reinterpret_cast<const float*>(&mq4);
-    float samp[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int r = r0 + e;
-        if (r >= R) continue;
-        float v[NS];
-#pragma unroll
-        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
-        float xi[NS + 1];
-        gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.rk, xi);
-        gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
-#pragma unroll
-        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
-    }
-    *reinterpret_cast<float4*>(q + off) = q4;
-    *reinterpret_cast<float4*>(p + off) = v4[0];
-#pragma unroll
-    for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
-    if (flags & kDoSample)
-        *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
-            make_float4(samp[0], samp[1], samp[2], samp[3]);
-    if (op_kind == kOpTf32) {
-        float* t = static_cast<float*>(op_hi);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) t[(int64_t)(r0 + e) * Np + i] = to_tf32(qa[e]);
-    } else if (op_kind == kOpBf16x2) {
-        __nv_bfloat16* h = static_cast<__nv_bfloat16*>(op_hi);
-        __nv_bfloat16* l = static_cast<__nv_bfloat16*>(op_lo);
+        float* qa = reinterpret_cast<float*>(&q4);
+        const float* mqa = reinterpret_cast<const float*>(&mq4);
+        float samp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(qa[e]);
-            h[(int64_t)(r0 + e) * Np + i] = hb;
-            l[(int64_t)(r0 + e) * Np + i] = __float2bfloat16_rn(qa[e] - __bfloat162float(hb));
+            const int r = r0 + e;
+            if (r >= R) continue;
+            float v[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+            float xi[NS + 1];
+            gle_normals<NS>(kappa, (uint32_t)i, (uint32_t)r + g.roff, g.rk, xi);
+            gle_fused<NS>(qa[e], v, mqa[e], g, xi, flags, observable, samp[e]);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+        }
+        *reinterpret_cast<float4*>(q + off) = q4;
+        *reinterpret_cast<float4*>(p + off) = v4[0];
+#pragma unroll
+        for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
+        if (flags & kDoSample)
+            *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
+                make_float4(samp[0], samp[1], samp[2], samp[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) qn[e] = qa[e];
+    }
+    if (op_kind == kOpNone) return;               // uniform over the grid
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tq[c0 + e][k] = qn[e];
+    __syncthreads();
+    const int ii = i0 + lane;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int rl = warp * 4 + m;              // replica within the tile
+        const int r = rp + rl;
+        if (r >= Rp || ii >= N) continue;
+        const float x = tq[rl][lane];
+        if (op_kind == kOpTf32) {
+            static_cast<float*>(op_hi)[(int64_t)r * Np + ii] = to_tf32(x);
+        } else {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+            static_cast<__nv_bfloat16*>(op_hi)[(int64_t)r * Np + ii] = hb;
+            static_cast<__nv_bfloat16*>(op_lo)[(int64_t)r * Np + ii] =
+                __float2bfloat16_rn(x - __bfloat162float(hb));
         }
     }
 }
@@ -101,8 +116,8 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
                              cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((N + 31) / 32), (unsigned)((Rp / 4 + 7) / 8));
-    cfg.blockDim = dim3(32, 8);
+    cfg.gridDim = dim3((unsigned)((N + 31) / 32), (unsigned)((Rp + 31) / 32));
+    cfg.blockDim = dim3(256, 1);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
