@@ -366,10 +366,6 @@ inline float bf16_to_f(uint16_t h) {
     std::memcpy(&f, &u, 4);
     return f;
 }
-// Offset of element (i, j) of an Np x Np matrix stored as [Np/128][Np/ks][128][ks].
-inline size_t blocked_index(int64_t i, int64_t j, int64_t Np, int64_t ks) {
-    return (size_t)((((i / 128) * (Np / ks) + j / ks) * 128 + (i % 128)) * ks + (j % ks));
-}
 
 inline float tf32_rna(float f) {
     uint32_t u;
