@@ -132,8 +132,13 @@ fth_status fth_workspace_size(const fth_matrix* M, const fth_gle* gle, const fth
 /* Validate the problem, build T and S in FP64 on the host, copy M into the workspace
  * (converted/rounded for the chosen precision) and zero the state: q = p = s = 0 at a
  * step boundary.  `workspace` must be 256-byte aligned device memory of at least
- * fth_workspace_size() bytes.  Enqueues its copies on opt->stream.
- * Errors: INVALID_ARG, NOT_SPD (a diagonal entry <= 0), UNSUPPORTED, WORKSPACE, CUDA. */
+ * fth_workspace_size() bytes.  Enqueues its copies on opt->stream and returns after they
+ * completed.  A dense M is checked and converted on the device: read in place when
+ * M->on_device (it must stay valid until fth_create returns), else copied in row chunks
+ * through the part of the workspace that the state will occupy.  A host M is read and
+ * not kept.
+ * Errors: INVALID_ARG (also non-finite entries), NOT_SPD (a diagonal entry <= 0),
+ * UNSUPPORTED, WORKSPACE, CUDA. */
 fth_status fth_create(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
                       void* workspace, size_t workspace_bytes, fth_ctx** out);
 
