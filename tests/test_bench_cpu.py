@@ -1,0 +1,69 @@
+"""Host-side pieces of bench.py: the roofline arithmetic and the traffic table lookup
+(no GPU)."""
+import hashlib
+import os
+import re
+import sys
+
+import pytest
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), ".."))
+sys.path.insert(0, ROOT)
+bench = pytest.importorskip("bench")
+
+KNOWN = {"force_tc", "syrk_tc", "gle_dense", "csr_step", "pair_accum", "pool_force", "pool_gle",
+         "pool_accum", "fp64_dense"}
+
+
+def test_traffic_table_format():
+    lines = open(os.path.join(ROOT, "profiles", "traffic.txt")).read().splitlines()
+    rows = [ln.split() for ln in lines if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for f in rows:
+        assert len(f) == 4, f
+        kernel, src, digest, nbytes = f
+        assert kernel in KNOWN, kernel
+        assert os.path.exists(os.path.join(ROOT, src)), src
+        assert re.fullmatch(r"[0-9a-f]{16}", digest), digest
+        assert int(nbytes) > 0
+
+
+def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source v1\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        f"# header\nforce_tc  k.cu  {digest}  12345\ngle_dense  k.cu  0000000000000000  7\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic("force_tc") == 12345
+    assert bench._traffic("gle_dense") is None          # stale capture: source changed
+    assert bench._traffic("csr_step") is None           # never captured
+    src.write_text("kernel source v2\n")
+    assert bench._traffic("force_tc") is None
+
+
+class _Wl:
+    precision = "tf32"
+
+    def work(self, cls, info):
+        return {"gle_dense": ("hbm", 62.9e6), "force_tc": ("tensor", 8.59e9)}[cls]
+
+
+def test_roofline_picks_the_dominant_kernel_and_divides_by_its_peak():
+    peaks = {"hbm_gbs": 6778.0, "bf16_tflops": 1873.2, "bf16_tflops_sustained": 1678.5}
+    # force: 100 launches, 2.5 ms in all (25 us each); GLE: 100 launches, 2.0 ms
+    prof = {"force_tc": (2.5, 100), "gle_dense": (2.0, 100)}
+    out = bench.roofline(prof, _Wl(), {}, peaks, "measured")
+    assert out["kernel"] == "force_tc" and out["bound"] == "tensor"
+    achieved = 8.59e9 / 25e-6 / 1e12
+    assert out["achieved"] == pytest.approx(achieved)
+    assert out["peak"] == pytest.approx(1678.5 * 1.1 / 2.25)
+    assert out["frac"] == pytest.approx(achieved / (1678.5 * 1.1 / 2.25))
+    assert out["share"] == {"force_tc": pytest.approx(2.5 / 4.5, abs=1e-4),
+                            "gle_dense": pytest.approx(2.0 / 4.5, abs=1e-4)}
+    prof = {"force_tc": (1.0, 100), "gle_dense": (2.0, 100)}
+    out = bench.roofline(prof, _Wl(), {}, peaks, "measured")
+    assert out["kernel"] == "gle_dense" and out["bound"] == "hbm"
+    assert out["achieved"] == pytest.approx(62.9e6 / 20e-6 / 1e9)
+    assert out["frac"] == pytest.approx(out["achieved"] / 6778.0)
