@@ -959,7 +959,11 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
             uint8_t* stage = c->ws + L.off_q0;
             const size_t span = L.total - L.off_q0;
             const size_t row_bytes = (size_t)N * esz_in;
-            const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)(span / row_bytes)));
+            if (span < row_bytes) {   // cannot happen: the state planes alone hold >= 16 N bytes
+                c->last_error = "workspace too small to stage a row of M";
+                return bail(FTH_E_WORKSPACE);
+            }
+            const int64_t rows = std::min<int64_t>(N, (int64_t)(span / row_bytes));
             for (int64_t r0 = 0; r0 < N; r0 += rows) {
                 const int64_t nr = std::min<int64_t>(rows, N - r0);
                 FTH_CK_C(cudaMemcpyAsync(stage, static_cast<const uint8_t*>(Min->values) + (size_t)r0 * row_bytes,
