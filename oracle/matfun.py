@@ -88,6 +88,40 @@ def cheb_apply(rowptr, col, val, n, coeffs, a, b, cols) -> np.ndarray:
     return out
 
 
+def fn_elements_sparse(rowptr, col, val, n, fns, pairs, degree=400, interval=None):
+    """Elements p_k(M)_ij for several functions at once by the Chebyshev route (one
+    three-term recurrence over the unit vectors e_j, shared by all of them).
+
+    fns: callables on arrays of eigenvalues.  Returns (values [len(fns), len(pairs)],
+    tails), tails[k] = sum of |c| over the last 10 % of function k's coefficients."""
+    if interval is None:
+        a, b = gershgorin(rowptr, col, val, n)
+        pad = 1e-3 * (b - a)
+        a, b = a - pad, b + pad
+    else:
+        a, b = interval
+    coeffs = [cheb_coeffs(fn, a, b, degree) for fn in fns]
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    js = np.unique(pairs[:, 1])
+    A = sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col), np.asarray(rowptr)),
+                      shape=(n, n))
+    alpha = 2.0 / (b - a)
+    beta = -(b + a) / (b - a)
+    V0 = np.zeros((n, len(js)))
+    V0[js, np.arange(len(js))] = 1.0
+    V1 = alpha * (A @ V0) + beta * V0
+    outs = [c[0] * V0 + c[1] * V1 for c in coeffs]
+    for k in range(2, degree + 1):
+        V2 = 2.0 * (alpha * (A @ V1) + beta * V1) - V0
+        for o, c in zip(outs, coeffs):
+            o += c[k] * V2
+        V0, V1 = V1, V2
+    where = {int(j): k for k, j in enumerate(js)}
+    vals = np.array([[o[int(i), where[int(j)]] for i, j in pairs] for o in outs])
+    tails = [float(np.sum(np.abs(c[int(0.9 * len(c)):]))) for c in coeffs]
+    return vals, tails
+
+
 def g_elements_sparse(rowptr, col, val, n, T, S, dt, pairs, degree=256, observable=0,
                       interval=None):
     """Elements g(M)_ij for the given pairs by the Chebyshev route.

@@ -67,3 +67,39 @@ def test_roofline_picks_the_dominant_kernel_and_divides_by_its_peak():
     assert out["kernel"] == "gle_dense" and out["bound"] == "hbm"
     assert out["achieved"] == pytest.approx(62.9e6 / 20e-6 / 1e9)
     assert out["frac"] == pytest.approx(out["achieved"] / 6778.0)
+
+
+def test_sampled_exact_target_agrees_with_the_eigendecomposition():
+    """The lattice route (Chebyshev on a sample of elements) against U diag(g) U^T on a
+    lattice small enough for eigh: fed the exact expected values it reports zero error."""
+    import numpy as np
+    import fth_synth as syn
+    from oracle import gle
+
+    L = 8
+    n = L ** 3
+    rowptr, col, val = syn.lattice_csr(L, seed=3)
+    val64 = val.astype(np.float32).astype(np.float64)
+    a, c = syn.random_gle(4, seed=4, rate=2.0)
+    dt = 0.1 / np.sqrt(14.5)
+
+    class _Lattice:
+        seed = 5
+        fit = {"kind": "fermi", "params": [2.0, 7.0]}
+
+        def __init__(self):
+            self.a_p, self.c_p, self.dt = a, c, dt
+
+        def oracle_matrix(self):
+            return {"csr": (rowptr, col, val64, n)}
+
+    pairs = np.concatenate([syn.diag_pairs(n), syn.lattice_nn_pairs(L)])
+    lam, U = np.linalg.eigh(syn.csr_to_dense(rowptr, col, val64, n))
+    T, S = gle.propagator(a, c, dt)
+    gm = gle.mode_response_mean(lam, T, S, dt, 0, 100)
+    GM = np.einsum("kj,kj->k", U[pairs[:, 0]] * gm[None, :], U[pairs[:, 1]])
+    out = bench.exact_target_sampled(_Lattice(), pairs, GM, np.full(len(pairs), 1e-3), 100, 1.0,
+                                     nsample=8, degree=300)
+    assert out["chebyshev_tail"] < 1e-10
+    assert out["rel_err"] < 1e-9
+    assert out["sigma_rel"] > 0 and out["steps_to_1e-3"] > 0

@@ -47,6 +47,29 @@ def test_chebyshev_route_matches_eigendecomposition():
     assert np.allclose(vals, want, atol=1e-10)
 
 
+def test_multi_function_chebyshev_route_matches_eigendecomposition():
+    """Several functions through one shared recurrence: the stationary response g, the
+    exact expected running mean after 50 samples and a Fermi function, each against the
+    eigendecomposition."""
+    L = 6
+    rowptr, col, val = syn.lattice_csr(L, seed=7)
+    n = L ** 3
+    a, c = syn.random_gle(4, seed=8, rate=2.0)
+    dt = 0.1 / np.sqrt(14.5)
+    T, S = gle.propagator(a, c, dt)
+    fns = [lambda x: gle.mode_response(x, T, S, dt),
+           lambda x: gle.mode_response_mean(x, T, S, dt, 0, 50),
+           lambda x: matfun.f_scalar("fermi", x, (2.0, 7.0))]
+    pairs = np.concatenate([syn.diag_pairs(n)[:10], syn.lattice_nn_pairs(L)[:10]])
+    vals, tails = matfun.fn_elements_sparse(rowptr, col, val, n, fns, pairs, degree=300)
+    Md = syn.csr_to_dense(rowptr, col, val, n)
+    lam, U = np.linalg.eigh(Md)
+    for k, fn in enumerate(fns):
+        ref = (U * fn(lam)[None, :]) @ U.T
+        assert tails[k] < 1e-10
+        assert np.allclose(vals[k], [ref[i, j] for i, j in pairs], atol=1e-10)
+
+
 def test_lattice_spectrum_inside_gershgorin_interval():
     rowptr, col, val = syn.lattice_csr(5, seed=7)
     lo, hi = matfun.gershgorin(rowptr, col, val, 125)
