@@ -608,8 +608,9 @@ def run_ragged(args, rank, world, local):
     hs = [g.add(**dict(wl.problem(k, seed_shift=1), M=pinned[k]), replica_offset=rank * wl.R)
           for k in range(wl.count)]
     g.run(steps)
+    read = {}
     for k, h in enumerate(hs):
-        g.elements(h, wl.pairs[k])
+        read[k] = g.elements(h, wl.pairs[k])
     t_e2e = time.perf_counter() - t0
     g.close()
     del pinned
@@ -639,9 +640,52 @@ def run_ragged(args, rank, world, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ragged(wl)
+        line["cpu_baseline"]["exact"] = exact_target_ragged(wl, read, steps, ms / steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def exact_target_ragged(wl, read, steps, ms_per_step, nsample=8):
+    """exact_target for the pool: on a seeded sample of problems, each problem's exact
+    values by the oracle's eigendecomposition (g, the expected running mean after `steps`
+    samples, f) at its tracked pairs, against the values and error bars the end-to-end
+    pool returned (`read[k]` = (values, errbars) of problem k).  Norms over the sample's
+    elements together; all problems advance one step per pool step, so the time to 1e-3
+    is in pool steps."""
+    from oracle import gle, matfun
+    t0 = time.perf_counter()
+    pick = np.random.default_rng(wl.seed + 1).choice(wl.count, size=nsample, replace=False)
+    T, S = gle.propagator(wl.a_p, wl.c_p, wl.dt)
+    fk, fp = wl.fit["kind"], tuple(wl.fit.get("params", ()))
+    G, GM, F, V, E, D = [], [], [], [], [], []
+    for k in pick:
+        k = int(k)
+        lam, U = np.linalg.eigh(wl.mats[k].astype(np.float64))
+        pr = wl.pairs[k]
+        a, b = U[pr[:, 0]], U[pr[:, 1]]
+        for out, d in ((G, gle.mode_response(lam, T, S, wl.dt)),
+                       (GM, gle.mode_response_mean(lam, T, S, wl.dt, 0, steps)),
+                       (F, matfun.f_scalar(fk, lam, fp))):
+            out.append(np.einsum("kj,kj->k", a * d[None, :], b))
+        V.append(read[k][0])
+        E.append(read[k][1])
+        D.append(pr[:, 0] == pr[:, 1])
+    G, GM, F, V, E, D = (np.concatenate(x) for x in (G, GM, F, V, E, D))
+    ng = float(np.linalg.norm(G))
+    sig = float(np.linalg.norm(E)) / ng
+    sig_d = float(np.linalg.norm(E[D]) / np.linalg.norm(G[D]))
+    t_all, t_d = steps * (sig / 1e-3) ** 2, steps * (sig_d / 1e-3) ** 2
+    return {
+        "sample": f"{nsample} of {wl.count} problems (seeded), {len(G)} tracked elements",
+        "eigh_s": time.perf_counter() - t0, "steps": steps,
+        "rel_err": float(np.linalg.norm(V - GM)) / ng, "sigma_rel": sig,
+        "transient": float(np.linalg.norm(GM - G)) / ng,
+        "fit_bias": float(np.linalg.norm(G - F) / np.linalg.norm(F)),
+        "time_to_1e-3_s": t_all * ms_per_step / 1e3, "steps_to_1e-3": t_all,
+        "sigma_rel_diag": sig_d, "steps_to_1e-3_diag": t_d,
+        "time_to_1e-3_diag_s": t_d * ms_per_step / 1e3,
+    }
 
 
 def cpu_baseline_ragged(wl, budget_s=CPU_BUDGET_S, nsample=16, steps=None):

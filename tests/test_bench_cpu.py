@@ -103,3 +103,35 @@ def test_sampled_exact_target_agrees_with_the_eigendecomposition():
     assert out["chebyshev_tail"] < 1e-10
     assert out["rel_err"] < 1e-9
     assert out["sigma_rel"] > 0 and out["steps_to_1e-3"] > 0
+
+
+def test_ragged_exact_target_reports_zero_error_for_the_exact_values():
+    import numpy as np
+    import fth_synth as syn
+    from oracle import gle
+
+    a, c = syn.random_gle(4, seed=9, rate=3.0)
+
+    class _Ragged:
+        seed, count = 11, 3
+        fit = {"kind": "inv_sqrt", "params": []}
+
+        def __init__(self):
+            self.a_p, self.c_p, self.dt = a, c, 0.01
+            self.mats = [syn.dense_spd(n, 1.0, 100.0, seed=20 + n)[0].astype(np.float32)
+                         for n in (40, 64, 100)]
+            self.pairs = [np.concatenate([syn.diag_pairs(m.shape[0]), syn.random_pairs(m.shape[0], 8, seed=1)])
+                          for m in self.mats]
+
+    wl = _Ragged()
+    T, S = gle.propagator(a, c, 0.01)
+    read = {}
+    for k, m in enumerate(wl.mats):
+        lam, U = np.linalg.eigh(m.astype(np.float64))
+        gm = gle.mode_response_mean(lam, T, S, 0.01, 0, 300)
+        pr = wl.pairs[k]
+        v = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
+        read[k] = (v, np.full(len(pr), 1e-3))
+    out = bench.exact_target_ragged(wl, read, 300, 0.25, nsample=2)
+    assert out["rel_err"] < 1e-12
+    assert out["sigma_rel"] > 0 and out["time_to_1e-3_s"] > 0 and out["fit_bias"] > 0
