@@ -808,8 +808,11 @@ def run_serving(args, rank, world, local):
     wall = srv.clock() - c0
     lat, states, rsteps, relerr = [], {}, [], []
     example = None
+    served = {}
     for j, rid in enumerate(ids):
         info, v, e = srv.result(rid)
+        if v is not None and info["state"] in ("done", "budget"):
+            served[j] = (v, e, info["steps"])
         if v is not None and example is None and j in wl.lattice_inv_sqrt:
             # one returned element of a lattice x^-1/2 request
             example = {"request": j, "element": [int(x) for x in wl.reqs[j]["pairs"][0]],
@@ -838,6 +841,7 @@ def run_serving(args, rank, world, local):
         "throughput": {"requests_per_s": len(lat) / wall, "replica_steps_per_s": replica_steps / wall,
                        "wall_s": wall},
         "retired_rel_err": {"median": float(np.median(relerr)) if relerr else None},
+        "served_vs_exact": serving_exact(wl, served) if rank == 0 else None,
         "example_result": example,
         "gpu_launches": launches, "clocks": clk,
         "e2e": {"value": p99, "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -847,6 +851,36 @@ def run_serving(args, rank, world, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_exact(wl, served, nsample=6):
+    """Served results against the oracle: on a seeded sample of the retired dense requests,
+    each request's exact expected running mean after its own number of samples (FP64
+    eigendecomposition, per-mode response of its GLE) at its tracked elements; the
+    normwise relative error of the served values and their z-scores against it."""
+    from oracle import gle
+    dense = sorted(j for j in served if "M" in wl.reqs[j])
+    if not dense:
+        return None
+    t0 = time.perf_counter()
+    pick = np.random.default_rng(wl.seed + 2).choice(dense, size=min(nsample, len(dense)),
+                                                     replace=False)
+    z, num, den = [], 0.0, 0.0
+    for j in pick:
+        r = wl.reqs[int(j)]
+        v, e, steps = served[int(j)]
+        lam, U = np.linalg.eigh(np.asarray(r["M"], dtype=np.float64))
+        T, S = gle.propagator(r["a_p"], r["c_p"], r["dt"])
+        gm = gle.mode_response_mean(lam, T, S, r["dt"], 0, int(steps))
+        pr = np.asarray(r["pairs"])
+        want = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
+        num += float(np.sum((v - want) ** 2))
+        den += float(np.sum(want ** 2))
+        z.append((v - want) / e)
+    z = np.abs(np.concatenate(z))
+    return {"requests": int(len(pick)), "elements": int(z.size), "rel_err": (num / den) ** 0.5,
+            "max_abs_z": float(np.max(z)), "frac_abs_z_below_4": float(np.mean(z < 4.0)),
+            "eigh_s": time.perf_counter() - t0}
 
 
 # ---------------------------------------------------------------------- GPU arm

@@ -135,3 +135,38 @@ def test_ragged_exact_target_reports_zero_error_for_the_exact_values():
     out = bench.exact_target_ragged(wl, read, 300, 0.25, nsample=2)
     assert out["rel_err"] < 1e-12
     assert out["sigma_rel"] > 0 and out["time_to_1e-3_s"] > 0 and out["fit_bias"] > 0
+
+
+def test_serving_exact_scores_the_exact_values_at_zero():
+    import numpy as np
+    import fth_synth as syn
+    from oracle import gle
+
+    a, c = syn.random_gle(4, seed=12, rate=3.0)
+
+    class _Serving:
+        seed = 21
+
+        def __init__(self):
+            self.reqs = []
+            for n in (50, 80, 120):
+                M = syn.dense_spd(n, 1.0, 100.0, seed=n)[0].astype(np.float32)
+                pairs = np.concatenate([syn.diag_pairs(n)[:16], syn.random_pairs(n, 16, seed=n)])
+                self.reqs.append(dict(M=M, a_p=a, c_p=c, dt=0.01, pairs=pairs))
+            rowptr, col, val = syn.lattice_csr(4, seed=1)
+            self.reqs.append(dict(csr=(rowptr, col, val, 64), a_p=a, c_p=c, dt=0.01,
+                                  pairs=syn.diag_pairs(64)[:4]))
+
+    wl = _Serving()
+    T, S = gle.propagator(a, c, 0.01)
+    served = {}
+    for j, r in enumerate(wl.reqs[:3]):
+        lam, U = np.linalg.eigh(r["M"].astype(np.float64))
+        gm = gle.mode_response_mean(lam, T, S, 0.01, 0, 400)
+        pr = r["pairs"]
+        v = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
+        served[j] = (v, np.full(len(pr), 1e-3), 400)
+    served[3] = (np.zeros(4), np.ones(4), 400)          # a lattice request: not sampled
+    out = bench.serving_exact(wl, served, nsample=3)
+    assert out["requests"] == 3 and out["elements"] == 96
+    assert out["rel_err"] < 1e-12 and out["max_abs_z"] < 1e-6 and out["frac_abs_z_below_4"] == 1.0
