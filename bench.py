@@ -38,6 +38,8 @@ if ROOT not in sys.path:
 import fth_synth as syn  # noqa: E402
 
 METRIC, UNIT = "GLE replica-steps/s", "replica-steps/s"
+# arithmetic of the force contraction (FP32 accumulation everywhere but fp64)
+DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 CPU_BUDGET_S = 15.0
 REF_BUDGET_S = 90.0
 
@@ -621,7 +623,7 @@ def run_ragged(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
         "config": {"workload": wl.label, "problems": wl.count, "sum_n": int(wl.sizes.sum()),
                    "sum_n2": int(np.sum(wl.sizes.astype(np.int64) ** 2)),
                    "replicas_per_problem": wl.R, "precision": "bf16x3",
@@ -806,7 +808,7 @@ def run_serving(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     wall = srv.clock() - c0
-    lat, states, rsteps, relerr = [], {}, [], []
+    lat, states, rsteps, relerr, met = [], {}, [], [], []
     example = None
     served = {}
     for j, rid in enumerate(ids):
@@ -820,9 +822,16 @@ def run_serving(args, rank, world, local):
         states[info["state"]] = states.get(info["state"], 0) + 1
         if info["state"] in ("done", "budget"):
             lat.append(info["t_done"] - c0 - wl.arrivals[j])
+            met.append(info["state"] == "done")
             rsteps.append(info["steps"])
             relerr.append(info["rel_err"])
     lat = np.asarray(lat)
+    met = np.asarray(met, dtype=bool)
+
+    def pct(x):
+        return ({"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)),
+                 "count": int(x.size)} if x.size else {"p50": None, "p99": None, "count": 0})
+
     replica_steps = 32 * float(np.sum(rsteps))
     srv.close()
     p50 = float(np.percentile(lat, 50)) if lat.size else None
@@ -830,14 +839,16 @@ def run_serving(args, rank, world, local):
     line = {
         "metric": "p99 request latency", "value": p99, "unit": "s", "n_gpus": world,
         "steps": steps_total, "warmup": 0, "ms_per_step": wall / max(steps_total, 1) * 1e3,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
         "data": "synthetic",
         "config": {"workload": wl.label, "requests": len(wl.reqs), "submitted": len(ids),
                    "states": states, "chunk_steps": 1000, "min_blocks": 4,
                    "workspace_gb": args.serve_gb, "peak_used_gb": peak_used / 2 ** 30,
                    "l2": "resident working set of all admitted requests >> L2"},
         "latency_s": {"p50": p50, "p99": p99, "mean": float(lat.mean()) if lat.size else None,
-                      "max": float(lat.max()) if lat.size else None},
+                      "max": float(lat.max()) if lat.size else None,
+                      "met_target": pct(lat[met]), "spent_budget": pct(lat[~met]),
+                      "share_met": float(met.mean()) if met.size else None},
         "throughput": {"requests_per_s": len(lat) / wall, "replica_steps_per_s": replica_steps / wall,
                        "wall_s": wall},
         "retired_rel_err": {"median": float(np.median(relerr)) if relerr else None},
@@ -871,7 +882,8 @@ def serving_exact(wl, served, nsample=6):
         v, e, steps = served[int(j)]
         lam, U = np.linalg.eigh(np.asarray(r["M"], dtype=np.float64))
         T, S = gle.propagator(r["a_p"], r["c_p"], r["dt"])
-        gm = gle.mode_response_mean(lam, T, S, r["dt"], 0, int(steps))
+        # the first pool step of a request is its prologue: steps - 1 samples
+        gm = gle.mode_response_mean(lam, T, S, r["dt"], 0, int(steps) - 1)
         pr = np.asarray(r["pairs"])
         want = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
         num += float(np.sum((v - want) ** 2))
@@ -996,7 +1008,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if wl.precision == "fp64" else "f32", "data": "synthetic",
+        "dtype": DTYPE[wl.precision], "data": "synthetic",
         "config": {"workload": wl.label, "n": wl.n, "replicas_per_gpu": wl.R,
                    "precision": wl.precision, "track": wl.track, "s": 4, "dt": wl.dt,
                    "block": wl.block, "mu": wl.mu, "fit_max_rel_err": wl.fit.get("max_rel_err"),

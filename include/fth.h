@@ -212,6 +212,17 @@ fth_status fth_profile_enable(fth_ctx* ctx, int enable);
  * launch counts recorded since the last read (arrays of FTH_K_CLASSES entries). */
 fth_status fth_profile_read(fth_ctx* ctx, double* ms, int64_t* launches);
 
+/* Test hook for the device timeout path (tensor-core dense contexts only).  With
+ * limit_ns > 0 the context's next force launches issue no operand copies, so the waits
+ * of their main loop, which nothing completes, give up after limit_ns: each CTA sets
+ * FTH_E_TIMEOUT in the context's error word, issues nothing more, frees its tensor
+ * memory and returns (nothing is in flight, so no GPU fault is possible).  The error
+ * word is sticky: fth_status_poll and fth_elements report FTH_E_TIMEOUT from then on,
+ * because the steps that ran without a force are not valid.  0 restores normal
+ * launches.  Errors: INVALID_ARG (limit above the 1 s bound), UNSUPPORTED (no
+ * tensor-core force in this context). */
+fth_status fth_test_stall(fth_ctx* ctx, uint64_t limit_ns);
+
 /* One dense FP32 fused launch that allocates nothing, for callers that cannot allocate
  * device memory: a plugin whose host framework owns all device memory through its own
  * pool, a real-time loop that must never enter an allocator, or code that can only pass
@@ -234,7 +245,8 @@ fth_status fth_profile_read(fth_ctx* ctx, double* ms, int64_t* launches);
  * every entry it reads, so nothing needs clearing.  Calls that overlap on the GPU (two
  * streams, or two host threads on one device) race on the array: serialise them.
  * Errors: INVALID_ARG (pointers, sizes, alignment), UNSUPPORTED when n * ldr exceeds the
- * array (4,194,304 floats), CUDA. */
+ * array (4,194,304 floats) or ldr exceeds 2,097,120 (65,535 tiles of 32 replicas), both
+ * checked before any device work, CUDA. */
 fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t ldm, float* q, float* p,
                                   float* s, int64_t replicas, int64_t ldr, int s_aux,
                                   const double* T, const double* S, double dt, uint64_t seed,

@@ -35,7 +35,8 @@ EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_g
            "fth_pool_stats", "fth_pool_profile", "fth_pool_progress", "fth_pool_last_error",
            "fth_pool_destroy", "fth_server_create", "fth_server_submit", "fth_server_step",
            "fth_server_result", "fth_server_clock", "fth_server_pool", "fth_server_last_error",
-           "fth_server_destroy", "fth_functional_bytes", "fth_functional_add", "fth_functional")
+           "fth_server_destroy", "fth_functional_bytes", "fth_functional_add", "fth_functional",
+           "fth_test_stall")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense", "fp64_noise")
 
@@ -141,6 +142,7 @@ def load(path: str = LIB_PATH):
         "fth_version": ([], ctypes.c_char_p),
         "fth_profile_enable": ([P, INT], INT),
         "fth_profile_read": ([P, P, P], INT),
+        "fth_test_stall": ([P, ctypes.c_uint64], INT),
         "fth_dense_step_noalloc": ([P, I64, I64, P, P, P, I64, I64, INT, P, P, D,
                                     ctypes.c_uint64, ctypes.c_uint32, INT, P, P], INT),
         "fth_pool_create": ([P, P, ctypes.c_size_t, P], INT),
@@ -366,6 +368,10 @@ class FTH:
 
     def poll(self):
         _check(load().fth_status_poll(self.ctx), self.ctx)
+
+    def test_stall(self, limit_ns: int):
+        """Test hook: later force launches end through the device timeout path."""
+        _check(load().fth_test_stall(self.ctx, int(limit_ns)), self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

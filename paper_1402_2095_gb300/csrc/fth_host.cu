@@ -1359,6 +1359,20 @@ fth_status fth_info(const fth_ctx* c, fth_info_t* info) {
     return FTH_OK;
 }
 
+fth_status fth_test_stall(fth_ctx* c, uint64_t limit_ns) {
+    if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
+    if (!is_tc(c) || !c->tcf) {
+        c->last_error = "fth_test_stall needs a tensor-core (TF32 or BF16X3) dense context";
+        return FTH_E_UNSUPPORTED;
+    }
+    if (limit_ns > 1000000000ull) {
+        c->last_error = "stall limit above the 1 s wait bound";
+        return FTH_E_INVALID_ARG;
+    }
+    tc_force_set_stall(c->tcf, limit_ns);
+    return FTH_OK;
+}
+
 fth_status fth_profile_enable(fth_ctx* c, int enable) {
     if (!c) return fail(nullptr, FTH_E_INVALID_ARG, "ctx is NULL");
     c->prof = enable != 0;

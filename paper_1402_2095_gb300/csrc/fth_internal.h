@@ -155,6 +155,9 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st);
 void tc_force_free(TcForce* tf);
+// Test hook: stall_ns > 0 makes later launches issue no copies and end through their
+// timeout path after stall_ns (see fth_test_stall); 0 restores normal launches.
+void tc_force_set_stall(TcForce* tf, uint64_t stall_ns);
 
 struct TcSyrk;
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);

@@ -45,15 +45,27 @@ struct TcMaps {
 };
 
 // a_blocks > 0: A is the blocked 3-D map with a_blocks K slices per row block.
+// stall_ns > 0 (test hook, fth_test_stall): the producer issues no copies and the
+// main-loop waits give up after stall_ns, so the launch ends through its timeout path
+// with nothing in flight; the drain and epilogue waits keep the full bound.
 template <int KIND, int BN, int STAGES>
 __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b_row,
                                             int nslices, uint8_t* stages, uint64_t* full,
                                             uint64_t* empty, uint64_t* done, uint32_t tmem,
                                             uint32_t* err, int slice0 = 0, int a_blocks = 0,
-                                            bool dep_wait = false) {
+                                            bool dep_wait = false, uint64_t stall_ns = 0) {
     using C = TcCfg<KIND, BN>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0 && lane == 0) {
+    const uint64_t loop_ns = stall_ns ? stall_ns : kWaitNs;
+    if (warp == 0 && lane == 0 && stall_ns) {
+        if (dep_wait) {
+            grid_dependency_wait();
+            allow_dependent_launch();
+        }
+        // nothing issued: a wait for the first release of slot 0, which nothing
+        // releases, runs out (as the MMA thread's wait for its first stage does)
+        if (nslices > 0) mbar_wait(&empty[0], 0, err, loop_ns);
+    } else if (warp == 0 && lane == 0) {
         // TMA producer.  With dep_wait (a programmatic dependent launch whose B operand
         // is written by the previous kernel) the A slices of the first ring fill, which
         // no earlier kernel writes, are issued before the grid dependency wait.
@@ -107,7 +119,7 @@ __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b
         bool ok = true;
         for (int kb = 0; kb < nslices; ++kb) {
             const int st = kb % STAGES;
-            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err)) {
+            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err, loop_ns)) {
                 ok = false;
                 break;
             }
@@ -192,14 +204,14 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int ldf, int N,
-                int Rp, int nslices, uint32_t* err) {
+                int Rp, int nslices, uint32_t* err, uint64_t stall_ns) {
     uint8_t* stages;
     uint64_t *full, *empty, *done;
     uint32_t tmem;
     tc_setup<KIND, BN, STAGES>(stages, full, empty, done, tmem);
     const int row0 = blockIdx.x * 128, col0 = blockIdx.y * BN;
     tc_mainloop<KIND, BN, STAGES>(maps, row0, col0, nslices, stages, full, empty, done, tmem, err,
-                                  0, nslices);
+                                  0, nslices, false, stall_ns);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -255,7 +267,7 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t local_saddr, uint32_t r
 template <int KIND, int BN, int STAGES, int KSPLIT>
 __global__ void __launch_bounds__(128, 1)
 tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int ldf,
-                       int N, int Rp, int nslices_total, uint32_t* err) {
+                       int N, int Rp, int nslices_total, uint32_t* err, uint64_t stall_ns) {
     constexpr int LDS = BN + 4;                 // padded row of the staged partial
     static_assert(STAGES * TcCfg<KIND, BN>::kStageBytes >= 128 * LDS * 4, "stage space");
     uint8_t* stages;
@@ -273,7 +285,7 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
     const int s0 = (nslices_total * kc) / KSPLIT;
     const int s1 = (nslices_total * (kc + 1)) / KSPLIT;
     tc_mainloop<KIND, BN, STAGES>(maps, row0, 0, s1 - s0, stages, full, empty, done, tmem, err,
-                                  s0, nslices_total, true);
+                                  s0, nslices_total, true, stall_ns);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -617,6 +629,7 @@ struct TcForce {
     int kind;
     bool wide;
     int64_t Np, Rp, N, R;
+    uint64_t stall_ns = 0;   // test hook: > 0 makes the launches end through their timeout path
 };
 
 struct TcSyrk {
@@ -682,7 +695,7 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
     cfg.numAttrs = 2;
     const int nslices = (int)(KIND == 1 ? tf->Np / 32 : tf->Np / 64);
     return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
-                              nslices, err);
+                              nslices, err, tf->stall_ns);
 }
 
 
@@ -700,7 +713,7 @@ cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* er
         auto kern = tc_force_kernel<K, kForceBN, kForceStages>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<grid, 128, sm, st>>>(tf->maps, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
-                                    (int)(tf->Np / 32), err);
+                                    (int)(tf->Np / 32), err, tf->stall_ns);
     } else {
         constexpr int K = 2;
         constexpr int S = 4;
@@ -708,12 +721,14 @@ cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* er
         auto kern = tc_force_kernel<K, kForceBN, S>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<grid, 128, sm, st>>>(tf->maps, MQ, (int)ldf, (int)tf->N, (int)tf->Rp,
-                                    (int)(tf->Np / 64), err);
+                                    (int)(tf->Np / 64), err, tf->stall_ns);
     }
     return cudaGetLastError();
 }
 
 void tc_force_free(TcForce* tf) { delete tf; }
+
+void tc_force_set_stall(TcForce* tf, uint64_t stall_ns) { tf->stall_ns = stall_ns; }
 
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld) {
     TcSyrk* ts = new TcSyrk();

@@ -22,6 +22,8 @@ namespace {
 // it until exit) and every call shares it.
 constexpr int64_t kNoallocScratch = int64_t(1) << 22;
 static __device__ __align__(256) float g_noalloc_mq[kNoallocScratch];
+// The element-wise step tiles replicas by 32 on the grid's y dimension (<= 65535).
+constexpr int64_t kNoallocMaxLdr = int64_t(65535) * 32;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -37,7 +39,8 @@ noalloc_force_kernel(const float* __restrict__ M, int64_t ldm, const float* __re
     __shared__ float Bs[BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+    // replica tiles on x (up to 2^31 - 1 blocks), row tiles on y (n <= 2^22 rows)
+    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
     float acc[4][4] = {};
     for (int k0 = 0; k0 < n; k0 += BK) {
         for (int e = tid; e < BM * BK; e += 256) {
@@ -101,7 +104,9 @@ extern "C" fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t 
     if (!M || !q || !p || (s_aux > 0 && !s) || !T || !S) return FTH_E_INVALID_ARG;
     if (n < 1 || ldm < n || replicas < 1 || ldr < replicas || (ldr % 4) != 0) return FTH_E_INVALID_ARG;
     if (s_aux < 0 || s_aux > 4 || !(dt > 0.0) || (mode != 0 && mode != 1)) return FTH_E_INVALID_ARG;
-    if (n * ldr > kNoallocScratch) return FTH_E_UNSUPPORTED;   // beyond the static scratch
+    // n * ldr floats must fit the static scratch (divide first, so absurd sizes cannot
+    // overflow), and the element-wise step's grid takes at most kNoallocMaxLdr replicas
+    if (ldr > kNoallocMaxLdr || ldr > kNoallocScratch / n) return FTH_E_UNSUPPORTED;
     const uintptr_t mis = reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(p) |
                           reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(sample);
     if (mis & 15u) return FTH_E_INVALID_ARG;                  // float4 state access
@@ -120,7 +125,7 @@ extern "C" fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t 
     set_round_keys(g);
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
 
-    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((ldr + 63) / 64));
+    dim3 grid((unsigned)((ldr + 63) / 64), (unsigned)((n + 63) / 64));
     noalloc_force_kernel<<<grid, 256, 0, strm>>>(M, ldm, q, ldr, mq, (int)n);
     if (cudaGetLastError() != cudaSuccess) return FTH_E_CUDA;
     const int flags = mode == 1 ? kDoStart : (kDoEnd | kDoStart | (sample ? kDoSample : 0));

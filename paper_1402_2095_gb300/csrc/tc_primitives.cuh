@@ -52,12 +52,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false (and the timeout bit set) if the phase did not complete in 1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+// Bounded wait; false (and the timeout bit set) if the phase did not complete within
+// limit_ns (1 s unless a test asks for less).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err,
+                                          uint64_t limit_ns = kWaitNs) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try(bar, parity)) {
-        if (global_ns() - t0 > kWaitNs) {
+        if (global_ns() - t0 > limit_ns) {
             atomicOr(err, kErrTimeout);
             return false;
         }

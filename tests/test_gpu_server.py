@@ -3,7 +3,10 @@
 Requests arrive while others run, are admitted when they fit, and are retired when
 their error bar meets their target.  Each retired result must be bit-identical to the
 same problem run alone in a pool for the same number of steps (its noise key is its own
-seed and the pool's arithmetic per problem does not depend on the mix).
+seed and the pool's arithmetic per problem does not depend on the mix), and equal to the
+FP64 oracle: on the same noise within the precision of the pool's force (BF16x3 dense,
+FP32 CSR), and within a few block error bars of the exact expected running mean
+(paper Eq. 6 for the fitted GLE's discrete response, from the zero state).
 """
 import numpy as np
 import pytest
@@ -149,4 +152,48 @@ def test_server_fails_requests_that_can_never_fit():
         srv.step()
     assert srv.result(ib)[0]["state"] == "failed"
     assert srv.result(ig)[0]["state"] in ("done", "budget")
+    srv.close()
+
+
+def test_served_results_match_the_oracle():
+    """A dense and a lattice request served together, retired on their step budget:
+    each served element against the oracle run on the same noise (same seed, same
+    number of samples) and against the exact expected running mean after the request's
+    own number of samples (z-scores of the block error bars)."""
+    from oracle import gle, matfun
+    from oracle.fth import OracleFTH
+    from paper_1402_2095_gb300 import Server
+    reqs = _requests()
+    chosen = [reqs[1], reqs[4]]                # dense n = 200 (BF16x3), lattice 5^3 (CSR)
+    srv = Server(1 << 27, replicas=32, max_problems=4, chunk_steps=100, min_blocks=2)
+    ids = [srv.submit(**kw, target=1e-9, max_steps=2000) for kw in chosen]
+    for _ in range(30):
+        c = srv.step()
+        if c["running"] == 0 and c["queued"] == 0:
+            break
+    for rid, kw, tol in zip(ids, chosen, (2e-3, 1e-4)):
+        info, v, e = srv.result(rid)
+        assert info["state"] == "budget" and info["steps"] == 2000
+        nsamples = info["steps"] - 1           # the first pool step is the prologue
+        if "M" in kw:
+            Mo = np.asarray(kw["M"], dtype=np.float32).astype(np.float64)
+            o = OracleFTH(M=Mo, a_p=kw["a_p"], c_p=kw["c_p"], dt=kw["dt"], replicas=32,
+                          seed=kw["seed"], block=kw["block"], pairs=kw["pairs"])
+        else:
+            rowptr, col, val, n = kw["csr"]
+            o = OracleFTH(csr=(rowptr, col, np.asarray(val, np.float32).astype(np.float64), n),
+                          a_p=kw["a_p"], c_p=kw["c_p"], dt=kw["dt"], replicas=32,
+                          seed=kw["seed"], block=kw["block"], pairs=kw["pairs"])
+            Mo = syn.csr_to_dense(rowptr, col, np.asarray(val, np.float32).astype(np.float64), n)
+        o.run(nsamples)
+        vo, eo = o.elements()
+        # same noise: the pool's force precision
+        assert np.max(np.abs(v - vo)) <= tol * np.max(np.abs(vo)), (rid, np.max(np.abs(v - vo)))
+        # exact expected running mean of the fitted GLE after nsamples samples
+        T, S = gle.propagator(kw["a_p"], kw["c_p"], kw["dt"])
+        pr = np.asarray(kw["pairs"])
+        want = matfun.g_mean_of_matrix(Mo, T, S, kw["dt"], 0, nsamples)[pr[:, 0], pr[:, 1]]
+        z = (v - want) / e
+        assert np.all(np.abs(z) < 4.5), (rid, z)
+        assert 0.3 < np.mean(z ** 2) < 3.0, (rid, np.mean(z ** 2))
     srv.close()

@@ -54,7 +54,15 @@ def test_noalloc_two_calls_match_fth_run():
     lib = binding.load()
     stream = torch.cuda.current_stream()
 
+    from oracle import gle
+    from oracle.fth import fused_step_elements
+    To, So = gle.propagator(a, c, dt)
+    elems = [(int(i), int(r)) for i, r in zip(g.integers(0, n, 40), g.integers(0, R, 40))]
+    state = (q0, p0, s0)
     for kappa in (1, 2):
+        # the oracle, one sampled (i, r) at a time, from the state before this call
+        qn, pn, sn, xn = fused_step_elements(M32.astype(np.float64), *state, To, So, dt, seed,
+                                             kappa, elems)
         ref.run(1)
         st = lib.fth_dense_step_noalloc(
             Md.data_ptr(), n, n, qd.data_ptr(), pd.data_ptr(), sd.data_ptr(), R, ldr, s_aux,
@@ -65,7 +73,15 @@ def test_noalloc_two_calls_match_fth_run():
         assert _rel(qd.cpu().numpy().T, ref.get_state("q")) <= 1e-5
         assert _rel(pd.cpu().numpy().T, ref.get_state("p")) <= 1e-5
         assert _rel(np.transpose(sd.cpu().numpy(), (2, 0, 1)), ref.get_state("s")) <= 1e-5
-        assert np.all(np.isfinite(sample.cpu().numpy()))
+        got_q, got_p = qd.cpu().numpy().T, pd.cpu().numpy().T
+        got_s = np.transpose(sd.cpu().numpy(), (2, 0, 1))
+        got_x = sample.cpu().numpy().T                 # p at the end of step kappa - 1
+        for k, (i, r) in enumerate(elems):
+            assert abs(got_q[r, i] - qn[k]) <= 1e-5 * (1 + abs(qn[k]))
+            assert abs(got_p[r, i] - pn[k]) <= 1e-5 * (1 + abs(pn[k]))
+            assert np.allclose(got_s[r, :, i], sn[k], rtol=1e-5, atol=1e-5)
+            assert abs(got_x[r, i] - xn[k]) <= 1e-5 * (1 + abs(xn[k]))
+        state = (got_q.astype(np.float64), got_p.astype(np.float64), got_s.astype(np.float64))
 
 
 def test_noalloc_rejects_sizes_beyond_scratch():
@@ -80,3 +96,41 @@ def test_noalloc_rejects_sizes_beyond_scratch():
                                     1028, 1028, 0, T.ctypes.data, S.ctypes.data, 0.01, 1, 1, 0,
                                     None, None)
     assert st == 3
+    # absurd sizes are refused without overflowing n * ldr
+    st = lib.fth_dense_step_noalloc(x.data_ptr(), 1 << 40, 1 << 40, x.data_ptr(), x.data_ptr(),
+                                    None, 1 << 40, 1 << 40, 0, T.ctypes.data, S.ctypes.data,
+                                    0.01, 1, 1, 0, None, None)
+    assert st == 3
+    # one row with more replicas than the element-wise step's grid takes (65,535 x 32)
+    st = lib.fth_dense_step_noalloc(x.data_ptr(), 1, 1, x.data_ptr(), x.data_ptr(), None,
+                                    1, 65535 * 32 + 4, 0, T.ctypes.data, S.ctypes.data, 0.01, 1,
+                                    1, 0, None, None)
+    assert st == 3
+
+
+def test_noalloc_widest_row_runs():
+    # n = 1 with the widest replica stride accepted (65,535 x 32): grids stay in range
+    import torch
+    from paper_1402_2095_gb300 import binding
+    lib = binding.load()
+    ldr = 65535 * 32
+    dev = torch.device("cuda")
+    M = torch.full((1, 1), 4.0, device=dev)
+    q = torch.ones(ldr, device=dev)
+    p = torch.zeros(ldr, device=dev)
+    sample = torch.zeros(ldr, device=dev)
+    T = np.eye(1)
+    S = np.zeros((1, 1))
+    st = lib.fth_dense_step_noalloc(M.data_ptr(), 1, 1, q.data_ptr(), p.data_ptr(), None, ldr,
+                                    ldr, 0, T.ctypes.data, S.ctypes.data, 0.01, 3, 1, 0,
+                                    sample.data_ptr(), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    # noise-free (S = 0, T = I) with M = 4 from q = 1, p = 0: the end half kicks
+    # p = -(dt/2) 4, the sample takes it, the start half kicks again and drifts q
+    dt = 0.01
+    p_end = -0.5 * dt * 4.0
+    p_new = 2 * p_end
+    q_new = 1.0 + dt * p_new
+    for t, want in ((sample, p_end), (p, p_new), (q, q_new)):
+        assert torch.allclose(t, torch.full_like(t, want), rtol=0, atol=1e-6)
