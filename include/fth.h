@@ -171,6 +171,44 @@ fth_status fth_functional_add(fth_ctx* ctx, const int64_t* pairs, const double* 
 /* Value (all accumulated samples, as fth_elements) and block error bar (NaN before two
  * complete blocks).  Synchronises the stream. */
 fth_status fth_functional(fth_ctx* ctx, int64_t id, double* value, double* errbar);
+
+/* The trace estimators with their weights built by the library: Tr O f(M) = <p^T O p>
+ * for a symmetric O of the context's order (dense or CSR, host or device buffers, FP32
+ * or FP64; entries on and above the diagonal are read, w = O_ii on (i, i) and 2 O_ij on
+ * (i < j), zero entries dropped), or Tr f(M) when O is NULL.  _terms gives the number of
+ * terms, so the caller can size the device buffer with fth_functional_bytes; _add then
+ * registers the functional as fth_functional_add does (same rules and errors, plus
+ * INVALID_ARG for an O that does not fit the context or has non-finite entries). */
+fth_status fth_functional_operator_terms(fth_ctx* ctx, const fth_matrix* O, int64_t* nterms);
+fth_status fth_functional_add_operator(fth_ctx* ctx, const fth_matrix* O, void* device_buffer,
+                                       size_t bytes, int64_t* id);
+
+/* Reusing one fitted GLE for other spectra (Sec. "The f-thermostat"): with
+ * A_p -> alpha A_p and C_p -> gamma C_p, the estimate for the input r M + m I is
+ * gamma f((r M + m I) / alpha^2).  fth_spectral_map gives (r, m) with r lo + m = lo_target
+ * and r hi + m = hi_target (the shift printed in the paper has its sign flipped; this is
+ * the corrected form).  fth_gle_scale writes (alpha A_p, gamma C_p); in and out may be the
+ * same struct.  Errors: INVALID_ARG. */
+fth_status fth_spectral_map(double lo, double hi, double lo_target, double hi_target, double* r,
+                            double* m);
+fth_status fth_gle_scale(const fth_gle* in, double alpha, double gamma, fth_gle* out);
+
+/* Inverse transforms of the paper's benchmarks, from the sampled elements (or trace) to
+ * the wanted ones:
+ *   LOG_SCALED    params {r}:    ln M = ln(r M) - I ln r (diagonal elements lose ln r;
+ *                                the trace loses n ln r; error bars unchanged);
+ *   EXP_SHIFTED   params {a, m}: exp(-a M) = exp(-a (M + m I)) e^{a m} (values and error
+ *                                bars times e^{a m});
+ *   POWER_SCALED  params {r, k}: f(M) = f(r M) r^-k for f(x) = x^k (values and error bars
+ *                                times r^-k).
+ * Elements: `pairs` (2k indices, as fth_elements) name the elements of values / errbars
+ * (errbars may be NULL), transformed in place.  Trace: n is the order.  Errors:
+ * INVALID_ARG. */
+enum fth_untransform_kind { FTH_U_LOG_SCALED = 0, FTH_U_EXP_SHIFTED = 1, FTH_U_POWER_SCALED = 2 };
+fth_status fth_untransform(int kind, const double* params, const int64_t* pairs, int64_t k,
+                           double* values, double* errbars);
+fth_status fth_untransform_trace(int kind, const double* params, int64_t n, double* value,
+                                 double* errbar);
 fth_status fth_set_state(fth_ctx* ctx, int plane, const double* host);
 
 /* Counters and configuration of a context. */
@@ -188,6 +226,81 @@ void fth_destroy(fth_ctx* ctx);
 /* The library's own O half-step constants in FP64: T = exp(-A_p dt/2) (Pade scaling
  * and squaring) and lower-triangular S with S S^T = C_p - T C_p T^T; (s+1)^2 each. */
 fth_status fth_gle_propagator(const fth_gle* gle, double dt, double* T, double* S);
+
+/* ----------------------------------------------------------------------------------
+ * GLE fitting (host, FP64; no device work).  The paper fits the drift A_p and the
+ * free-particle covariance C_p so that a normal mode of eigenvalue lambda = w^2 has
+ * <p^2>(w) = f(lambda) over the spectrum of M (Sec. "The f-thermostat", the fitting
+ * paragraph; Eq. 2, Eq. 4), starting from delta-like memory kernels and then refining the
+ * general form, under the requirements of Sec. "Results and benchmarks": follow f over
+ * the range, treat f below delta * max f as an upper bound only (the exponential-tail
+ * rule), and keep correlation times short.  The fitted response is that of this
+ * library's integrator at the given dt (stationary covariance of the sample-to-sample
+ * map of each mode), so it carries no finite-dt error.
+ * ---------------------------------------------------------------------------------- */
+enum fth_function {
+    FTH_F_INV_SQRT = 0,     /* x^(-1/2)                                      (no params) */
+    FTH_F_FERMI = 1,        /* 1 / (1 + exp(beta (x - mu)))         params: beta, mu     */
+    FTH_F_LOG = 2,          /* ln x (the range must have lambda_min > 1) (no params)     */
+    FTH_F_EXP = 3,          /* exp(-alpha x)                        params: alpha        */
+    FTH_F_POWER = 4         /* x^k                                  params: k            */
+};
+
+enum fth_fit_objective {
+    FTH_FIT_AUTO = 0,       /* ABS for FERMI, LOG otherwise                              */
+    FTH_FIT_LOG = 1,        /* residuals ln(gamma g / f): relative error                 */
+    FTH_FIT_ABS = 2         /* residuals (gamma g - f) / max f: absolute error           */
+};
+
+/* Options of fth_fit_gle.  A zeroed struct means: observable P, 120 grid points, 6
+ * starts, 400 iterations, delta 1e-3, no correlation-time penalty, seed 0, all host
+ * threads, objective AUTO.  Passing NULL gives the same with w_tau = 0.2. */
+typedef struct {
+    int observable;         /* enum fth_observable: the moment fitted                      */
+    int npts;               /* log-spaced grid points over [lambda_min, lambda_max]        */
+    int starts;             /* seeded delta-like starts                                    */
+    int max_iter;           /* Levenberg-Marquardt iterations per start                    */
+    double delta;           /* tail threshold, relative to max f over the grid             */
+    double w_tau;           /* weight of the penalty ln(max(1, tau_max / tau_ref)), tau_ref =
+                               2.5 / (sqrt(lambda_min) dt) samples (>= 0)                  */
+    uint64_t seed;          /* seed of the starts                                          */
+    int threads;            /* host threads running the starts (0: all)                    */
+    int objective;          /* enum fth_fit_objective                                      */
+} fth_fit_options;
+
+typedef struct {
+    double max_rel_err;     /* max |gamma g / f - 1| over grid points with f >= delta max f */
+    double rms_rel_err;     /* rms of the same                                             */
+    double max_abs_err;     /* max |gamma g - f| / max f over the whole grid               */
+    double tail_max;        /* max gamma g / max f where f < delta max f (0 if none)       */
+    double tau_max;         /* largest integrated correlation time of the sampled x^2 over
+                               the grid, in samples (steps)                                */
+    double lambda_tau_max;  /* eigenvalue where tau_max is reached                         */
+    double cost;            /* final least-squares cost                                    */
+    int64_t evaluations;    /* response evaluations over all starts                        */
+    int grid;               /* grid points                                                 */
+    int objective;          /* FTH_FIT_LOG or FTH_FIT_ABS, as used                         */
+} fth_fit_report;
+
+/* Fit a GLE with s auxiliary momenta (1 <= s <= 4) to f over [lambda_min, lambda_max]
+ * for time step dt; writes out (s, A_p, C_p, with the overall scale gamma folded into
+ * C_p) and, if report is not NULL, the fit's quality.  Deterministic for a given seed
+ * and option set.  Errors: INVALID_ARG (bad range, lambda_max dt^2 >= 4, parameters or
+ * options, f not finite or negative on the grid), UNSUPPORTED (no start gave a valid GLE). */
+fth_status fth_fit_gle(int f_kind, const double* f_params, double lambda_min, double lambda_max,
+                       int s, double dt, const fth_fit_options* opt, fth_gle* out,
+                       fth_fit_report* report);
+
+/* The exact per-mode response of this library's integrator for a GLE at time step dt:
+ * for each eigenvalue lambda[e] > 0, g[e] = stationary <x^2> of the sampled observable
+ * (x = p or q) and, if tau is not NULL, tau[e] = its integrated correlation time of x^2
+ * in samples, 1 + 2 sum_{l >= 1} corr(x^2(0), x^2(l)).  With U diag(g) U^T (M = U diag
+ * (lambda) U^T) this is the value the estimate converges to (Eq. 6 for the fitted GLE),
+ * and tau sets the block length the error bars need (blocks much longer than tau).
+ * Errors: INVALID_ARG (bad arguments, lambda dt^2 >= 4 where velocity Verlet has no
+ * stationary state, or a GLE whose chain has none). */
+fth_status fth_gle_response(const fth_gle* gle, double dt, int observable, const double* lambda,
+                            int64_t n, double* g, double* tau);
 
 /* Kernel classes reported by fth_profile_read. */
 enum fth_kernel_class {

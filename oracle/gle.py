@@ -163,6 +163,29 @@ def mode_response_mean_recursive(lams, T, S, dt, burnin: int, nsamples: int, obs
     return np.asarray(out)
 
 
+def x2_correlation_time(lam: float, T, S, dt, observable: int = 0, rel: float = 1e-17,
+                        max_lags: int = 10_000_000) -> float:
+    """Integrated correlation time, in samples, of x^2 for the sampled observable x of
+    one mode (x = p or q): tau = 1 + 2 sum_{l >= 1} corr(x^2(0), x^2(l)).  For the
+    Gaussian stationary chain the autocovariance of x^2 at lag l is 2 c(l)^2 with
+    c(l) = e_x^T G^l C e_x, so corr = (c(l) / c(0))^2; the lags are summed one by one
+    (w_{l+1} = G w_l from w_0 = C e_x) until a term falls below rel.  The variance of the
+    mean of x^2 over n samples tends to 2 c(0)^2 tau / n."""
+    idx = IP if observable == 0 else IQ
+    G, _ = mode_chain(lam, T, S, dt)
+    C = discrete_cov(lam, T, S, dt)
+    w = C[:, idx].copy()
+    c0 = w[idx]
+    total = 1.0
+    for _ in range(max_lags):
+        w = G @ w
+        term = (w[idx] / c0) ** 2
+        total += 2.0 * term
+        if term < rel:
+            return float(total)
+    raise RuntimeError("correlation sum did not converge")
+
+
 # ---------------------------------------------------------------- continuous limit
 def continuous_cov(lam: float, a_p, c_p) -> np.ndarray:
     """dt -> 0 stationary covariance of (q, p, s): A X + X A^T = D with

@@ -36,7 +36,9 @@ EXPORTS = ("fth_workspace_size", "fth_create", "fth_run", "fth_elements", "fth_g
            "fth_pool_destroy", "fth_server_create", "fth_server_submit", "fth_server_step",
            "fth_server_result", "fth_server_clock", "fth_server_pool", "fth_server_last_error",
            "fth_server_destroy", "fth_functional_bytes", "fth_functional_add", "fth_functional",
-           "fth_test_stall")
+           "fth_test_stall", "fth_fit_gle", "fth_gle_response", "fth_functional_operator_terms",
+           "fth_functional_add_operator", "fth_spectral_map", "fth_gle_scale", "fth_untransform",
+           "fth_untransform_trace")
 KERNEL_CLASSES = ("force_fp32", "force_tc", "gle_dense", "csr_step", "pair_accum", "syrk_fp32",
                   "syrk_tc", "flush", "fp64_dense", "fp64_noise")
 
@@ -106,6 +108,24 @@ class fth_request_info(ctypes.Structure):
 REQUEST_STATE = {0: "queued", 1: "running", 2: "done", 3: "budget", 4: "failed"}
 
 
+class fth_fit_options(ctypes.Structure):
+    _fields_ = [("observable", ctypes.c_int), ("npts", ctypes.c_int), ("starts", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("delta", ctypes.c_double), ("w_tau", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("threads", ctypes.c_int), ("objective", ctypes.c_int)]
+
+
+class fth_fit_report(ctypes.Structure):
+    _fields_ = [("max_rel_err", ctypes.c_double), ("rms_rel_err", ctypes.c_double),
+                ("max_abs_err", ctypes.c_double), ("tail_max", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("lambda_tau_max", ctypes.c_double),
+                ("cost", ctypes.c_double), ("evaluations", ctypes.c_int64), ("grid", ctypes.c_int),
+                ("objective", ctypes.c_int)]
+
+
+FUNCTION = {"inv_sqrt": 0, "fermi": 1, "log": 2, "exp": 3, "power": 4}
+FIT_OBJECTIVE = {"auto": 0, "log": 1, "abs": 2}
+
+
 class fth_info_t(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("samples", ctypes.c_int64),
                 ("accumulated", ctypes.c_int64), ("blocks", ctypes.c_int64),
@@ -143,6 +163,14 @@ def load(path: str = LIB_PATH):
         "fth_profile_enable": ([P, INT], INT),
         "fth_profile_read": ([P, P, P], INT),
         "fth_test_stall": ([P, ctypes.c_uint64], INT),
+        "fth_fit_gle": ([INT, P, D, D, INT, D, P, P, P], INT),
+        "fth_gle_response": ([P, D, INT, P, I64, P, P], INT),
+        "fth_functional_operator_terms": ([P, P, P], INT),
+        "fth_functional_add_operator": ([P, P, P, ctypes.c_size_t, P], INT),
+        "fth_spectral_map": ([D, D, D, D, P, P], INT),
+        "fth_gle_scale": ([P, D, D, P], INT),
+        "fth_untransform": ([INT, P, P, I64, P, P], INT),
+        "fth_untransform_trace": ([INT, P, I64, P, P], INT),
         "fth_dense_step_noalloc": ([P, I64, I64, P, P, P, I64, I64, INT, P, P, D,
                                     ctypes.c_uint64, ctypes.c_uint32, INT, P, P], INT),
         "fth_pool_create": ([P, P, ctypes.c_size_t, P], INT),
@@ -205,6 +233,43 @@ def gle_propagator(a_p, c_p, dt):
     S = np.zeros(ns * ns)
     _check(load().fth_gle_propagator(ctypes.byref(g), dt, T.ctypes.data, S.ctypes.data))
     return T.reshape(ns, ns), S.reshape(ns, ns)
+
+
+def fit_gle(kind, params, lam_min, lam_max, dt, s=4, *, observable="p", npts=120, starts=6,
+            max_iter=400, delta=1e-3, w_tau=0.2, seed=0, threads=0, objective="auto"):
+    """fth_fit_gle: (a_p, c_p, report dict) of the GLE fitted to f over [lam_min, lam_max]."""
+    o = fth_fit_options()
+    o.observable = OBSERVABLE[observable]
+    o.npts, o.starts, o.max_iter = int(npts), int(starts), int(max_iter)
+    o.delta, o.w_tau = float(delta), float(w_tau)
+    o.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    o.threads = int(threads)
+    o.objective = FIT_OBJECTIVE[objective]
+    par = np.ascontiguousarray(np.asarray(list(params) + [0.0] * 4, dtype=np.float64))
+    out = fth_gle()
+    rep = fth_fit_report()
+    _check(load().fth_fit_gle(FUNCTION[kind], par.ctypes.data, float(lam_min), float(lam_max),
+                              int(s), float(dt), ctypes.byref(o), ctypes.byref(out),
+                              ctypes.byref(rep)))
+    ns = out.s + 1
+    a = np.array(out.a_p[:ns * ns]).reshape(ns, ns)
+    c = np.array(out.c_p[:ns * ns]).reshape(ns, ns)
+    r = {f: getattr(rep, f) for f, _ in fth_fit_report._fields_}
+    r["objective"] = {1: "log", 2: "abs"}.get(r["objective"], r["objective"])
+    return a, c, r
+
+
+def gle_response(a_p, c_p, dt, lams, observable="p", tau=False):
+    """fth_gle_response: exact per-mode <x^2> of the integrator (and its correlation time
+    of x^2 in samples when tau=True) for each eigenvalue."""
+    g = make_gle(a_p, c_p)
+    lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lams, dtype=np.float64)))
+    out = np.zeros(lam.size)
+    t = np.zeros(lam.size) if tau else None
+    _check(load().fth_gle_response(ctypes.byref(g), float(dt), OBSERVABLE[observable],
+                                   lam.ctypes.data, lam.size, out.ctypes.data,
+                                   t.ctypes.data if tau else None))
+    return (out, t) if tau else out
 
 
 class FTH:
@@ -325,7 +390,7 @@ class FTH:
 
     def add_functional(self, pairs, weights):
         """Register L = sum_k w_k <x_i x_j> over tracked pairs (before the first sample);
-        returns its id.  See trace_terms() for Tr f(M) and Tr O f(M)."""
+        returns its id.  add_trace() builds the terms of Tr f(M) and Tr O f(M)."""
         import torch
         pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
@@ -339,6 +404,41 @@ class FTH:
         fid = ctypes.c_int64(-1)
         _check(L.fth_functional_add(self.ctx, pr.ctypes.data, w.ctypes.data, pr.shape[0], ptr,
                                     nbytes, ctypes.byref(fid)), self.ctx)
+        self._func_bufs.append(buf)
+        return int(fid.value)
+
+    def add_trace(self, O=None):
+        """Register Tr O f(M) = <p^T O p> (O symmetric: dense array, torch tensor, scipy
+        sparse matrix or csr=(rowptr, col, val, n) tuple; None: Tr f(M)); the weights are
+        built by the library (fth_functional_add_operator).  Returns the functional's id."""
+        import torch
+        L = load()
+        keep = []
+        optr = None
+        if O is not None:
+            try:
+                import scipy.sparse as sp
+                if sp.issparse(O):
+                    C = sp.csr_matrix(O)
+                    O = {"csr": (C.indptr, C.indices, C.data, C.shape[0])}
+            except ImportError:
+                pass
+            if isinstance(O, dict):
+                mat = _matrix_struct(csr=O["csr"], keep=keep)
+            elif isinstance(O, tuple):
+                mat = _matrix_struct(csr=O, keep=keep)
+            else:
+                mat = _matrix_struct(M=O, keep=keep)
+            optr = ctypes.byref(mat)
+        nt = ctypes.c_int64(0)
+        _check(L.fth_functional_operator_terms(self.ctx, optr, ctypes.byref(nt)), self.ctx)
+        nbytes = int(L.fth_functional_bytes(nt.value))
+        with torch.cuda.stream(self.stream):
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        fid = ctypes.c_int64(-1)
+        _check(L.fth_functional_add_operator(self.ctx, optr, ptr, nbytes, ctypes.byref(fid)),
+               self.ctx)
         self._func_bufs.append(buf)
         return int(fid.value)
 
@@ -657,27 +757,43 @@ class Server:
             pass
 
 
-# ---------------------------------------------------------------------- estimator helpers
-def trace_terms(n=None, O=None):
-    """(pairs, weights) of Tr f(M) = sum_i <p_i p_i> (O None; n = order) or of
-    Tr O f(M) = sum_ij O_ij <p_i p_j> for a symmetric O (dense array or scipy sparse):
-    O_ii on (i, i) and 2 O_ij on (i, j), i < j."""
-    if O is None:
-        idx = np.arange(int(n), dtype=np.int64)
-        return np.stack([idx, idx], axis=1), np.ones(int(n))
-    try:
-        import scipy.sparse as sp
-        if sp.issparse(O):
-            C = sp.triu(sp.coo_matrix(O)).tocoo()
-            i, j, v = C.row.astype(np.int64), C.col.astype(np.int64), C.data.astype(np.float64)
-            w = np.where(i == j, v, 2.0 * v)
-            keep = w != 0
-            return np.stack([i[keep], j[keep]], axis=1), w[keep]
-    except ImportError:
-        pass
-    A = np.asarray(O, dtype=np.float64)
-    i, j = np.triu_indices(A.shape[0])
-    v = A[i, j]
-    w = np.where(i == j, v, 2.0 * v)
-    keep = w != 0
-    return np.stack([i[keep], j[keep]], axis=1).astype(np.int64), w[keep]
+# ---------------------------------------------------------------------- transforms
+UNTRANSFORM = {"log": 0, "exp": 1, "power": 2}
+
+
+def spectral_map(spec, target):
+    """fth_spectral_map: (r, m) with r spec[0] + m = target[0], r spec[1] + m = target[1]."""
+    r, m = ctypes.c_double(), ctypes.c_double()
+    _check(load().fth_spectral_map(float(spec[0]), float(spec[1]), float(target[0]),
+                                   float(target[1]), ctypes.byref(r), ctypes.byref(m)))
+    return r.value, m.value
+
+
+def gle_scale(a_p, c_p, alpha=1.0, gamma=1.0):
+    """fth_gle_scale: (alpha A_p, gamma C_p)."""
+    g = make_gle(a_p, c_p)
+    _check(load().fth_gle_scale(ctypes.byref(g), float(alpha), float(gamma), ctypes.byref(g)))
+    ns = g.s + 1
+    return (np.array(g.a_p[:ns * ns]).reshape(ns, ns), np.array(g.c_p[:ns * ns]).reshape(ns, ns))
+
+
+def untransform(kind, params, pairs, values, errbars=None):
+    """fth_untransform: wanted elements from sampled ones ("log": params (r,), "exp":
+    (a, m), "power": (r, k)); returns (values, errbars) as new arrays."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+    v = np.array(values, dtype=np.float64, copy=True).reshape(-1)
+    e = None if errbars is None else np.array(errbars, dtype=np.float64, copy=True).reshape(-1)
+    par = np.ascontiguousarray(np.asarray(list(params) + [0.0] * 2, dtype=np.float64))
+    _check(load().fth_untransform(UNTRANSFORM[kind], par.ctypes.data, pr.ctypes.data, pr.shape[0],
+                                  v.ctypes.data, None if e is None else e.ctypes.data))
+    return v, e
+
+
+def untransform_trace(kind, params, n, value, errbar=None):
+    """fth_untransform_trace: the wanted trace (and its error bar) from the sampled one."""
+    par = np.ascontiguousarray(np.asarray(list(params) + [0.0] * 2, dtype=np.float64))
+    v = ctypes.c_double(float(value))
+    e = ctypes.c_double(float(errbar) if errbar is not None else 0.0)
+    _check(load().fth_untransform_trace(UNTRANSFORM[kind], par.ctypes.data, int(n),
+                                        ctypes.byref(v), ctypes.byref(e)))
+    return (v.value, e.value) if errbar is not None else v.value

@@ -657,7 +657,10 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
         fth_status st = force(c);
         if (st != FTH_OK) return st;
         const bool take = c->nsamp >= c->burnin;
-        const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0);
+        // the tcgen05 accumulation pass reads the samples as TF32: round them to nearest
+        const bool tf32_samples = is_tc(c) && L.track == FTH_TRACK_ALL;
+        const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0) |
+                          (take && tf32_samples ? kSampleTf32 : 0);
         if (take && c->nfill == 0) {
             st = claim_stack(c);
             if (st != FTH_OK) return st;
@@ -1210,6 +1213,114 @@ fth_status fth_functional_add(fth_ctx* c, const int64_t* pairs, const double* we
     c->funcs.push_back(std::move(f));
     *id = (int64_t)c->funcs.size() - 1;
     return FTH_OK;
+}
+
+// Terms of Tr O f(M) = <p^T O p> for a symmetric O of the context's order: w = O_ii on
+// (i, i) and 2 O_ij on (i, j), i < j, from the entries on and above the diagonal (the
+// lower triangle is the mirror and is not read); zero entries are dropped.  O NULL is the
+// identity (Tr f(M)).  A device O is copied to the host first.
+static fth_status operator_terms(fth_ctx* c, const fth_matrix* O, std::vector<int64_t>& pairs,
+                                 std::vector<double>& w) {
+    pairs.clear();
+    w.clear();
+    const int64_t n = c->L.N;
+    if (!O) {
+        for (int64_t i = 0; i < n; ++i) {
+            pairs.push_back(i);
+            pairs.push_back(i);
+            w.push_back(1.0);
+        }
+        return FTH_OK;
+    }
+    if (O->n != n || (O->kind != FTH_DENSE && O->kind != FTH_CSR) ||
+        (O->dtype != FTH_F32 && O->dtype != FTH_F64) || !O->values ||
+        (O->kind == FTH_CSR && (!O->rowptr || !O->colind || O->nnz < 0))) {
+        c->last_error = "operator: order, kind, dtype or pointers do not fit the context";
+        return FTH_E_INVALID_ARG;
+    }
+    const size_t esz = O->dtype == FTH_F64 ? 8 : 4;
+    const int64_t nv = O->kind == FTH_DENSE ? n * n : O->nnz;
+    std::vector<uint8_t> vals((size_t)nv * esz);
+    std::vector<int32_t> rp, ci;
+    const int32_t* rowptr = O->rowptr;
+    const int32_t* colind = O->colind;
+    if (O->on_device) {
+        FTH_CK(cudaMemcpy(vals.data(), O->values, vals.size(), cudaMemcpyDeviceToHost), "d2h O");
+        if (O->kind == FTH_CSR) {
+            rp.resize(n + 1);
+            ci.resize(O->nnz);
+            FTH_CK(cudaMemcpy(rp.data(), O->rowptr, rp.size() * 4, cudaMemcpyDeviceToHost), "d2h O");
+            FTH_CK(cudaMemcpy(ci.data(), O->colind, ci.size() * 4, cudaMemcpyDeviceToHost), "d2h O");
+            rowptr = rp.data();
+            colind = ci.data();
+        }
+    } else if (nv > 0) {
+        std::memcpy(vals.data(), O->values, vals.size());
+    }
+    auto value = [&](int64_t k) {
+        return esz == 8 ? reinterpret_cast<const double*>(vals.data())[k]
+                        : (double)reinterpret_cast<const float*>(vals.data())[k];
+    };
+    auto add = [&](int64_t i, int64_t j, double o) -> bool {
+        if (!std::isfinite(o)) return false;
+        if (o == 0.0) return true;
+        pairs.push_back(i);
+        pairs.push_back(j);
+        w.push_back(i == j ? o : 2.0 * o);
+        return true;
+    };
+    if (O->kind == FTH_DENSE) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = i; j < n; ++j)
+                if (!add(i, j, value(i * n + j))) {
+                    c->last_error = "operator: non-finite entry";
+                    return FTH_E_INVALID_ARG;
+                }
+    } else {
+        if (rowptr[0] != 0 || rowptr[n] != O->nnz) {
+            c->last_error = "operator: bad CSR row offsets";
+            return FTH_E_INVALID_ARG;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (rowptr[i + 1] < rowptr[i]) {
+                c->last_error = "operator: bad CSR row offsets";
+                return FTH_E_INVALID_ARG;
+            }
+            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                const int64_t j = colind[k];
+                if (j < 0 || j >= n) {
+                    c->last_error = "operator: CSR column out of range";
+                    return FTH_E_INVALID_ARG;
+                }
+                if (j >= i && !add(i, j, value(k))) {
+                    c->last_error = "operator: non-finite entry";
+                    return FTH_E_INVALID_ARG;
+                }
+            }
+        }
+    }
+    return FTH_OK;
+}
+
+fth_status fth_functional_operator_terms(fth_ctx* c, const fth_matrix* O, int64_t* nterms) {
+    if (!c || !nterms) return fail(c ? &c->last_error : nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    std::vector<int64_t> pairs;
+    std::vector<double> w;
+    const fth_status st = operator_terms(c, O, pairs, w);
+    if (st != FTH_OK) return st;
+    *nterms = (int64_t)w.size();
+    return FTH_OK;
+}
+
+fth_status fth_functional_add_operator(fth_ctx* c, const fth_matrix* O, void* device_buffer,
+                                       size_t bytes, int64_t* id) {
+    if (!c || !id) return fail(c ? &c->last_error : nullptr, FTH_E_INVALID_ARG, "NULL argument");
+    std::vector<int64_t> pairs;
+    std::vector<double> w;
+    const fth_status st = operator_terms(c, O, pairs, w);
+    if (st != FTH_OK) return st;
+    return fth_functional_add(c, pairs.data(), w.data(), (int64_t)w.size(), device_buffer, bytes,
+                              id);
 }
 
 fth_status fth_functional(fth_ctx* c, int64_t id, double* value, double* errbar) {

@@ -66,8 +66,11 @@ cudaError_t launch_dense_prepare(const void* src, int f64, int64_t n, int64_t r0
                                  int64_t Np, int layout, void* hi, void* lo, uint32_t* flags,
                                  cudaStream_t st);
 
-// Flags of the dense element-wise GLE kernel.
-enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4 };
+// Flags of the dense element-wise GLE kernel.  kSampleTf32: stage the samples rounded
+// to TF32 (round to nearest), because the tensor-core accumulation pass reads them as
+// kind::tf32 operands and the MMA drops the low 13 mantissa bits (truncation, a bias of
+// ~7e-4 per product otherwise).
+enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleTf32 = 8 };
 
 // Operand copies of q the element-wise kernel writes for the force GEMM.
 enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };

@@ -81,6 +81,10 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, i
         *reinterpret_cast<float4*>(p + off) = v4[0];
 #pragma unroll
         for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
+        if (flags & kSampleTf32) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) samp[e] = to_tf32(samp[e]);
+        }
         if (flags & kDoSample)
             *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
                 make_float4(samp[0], samp[1], samp[2], samp[3]);

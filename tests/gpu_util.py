@@ -62,3 +62,19 @@ def state_rel_err(g, o):
         got = g.get_state(name)
         errs.append(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
     return max(errs)
+
+
+def trace_terms(n=None, O=None):
+    """The tests' own (pairs, weights) of Tr f(M) = sum_i <p_i p_i> (O None; n = order)
+    or Tr O f(M) = sum_ij O_ij <p_i p_j> for a symmetric O (dense array or scipy sparse):
+    O_ii on (i, i) and 2 O_ij on (i, j), i < j -- to check the library's own weights."""
+    import scipy.sparse as sp
+    if O is None:
+        idx = np.arange(int(n), dtype=np.int64)
+        return np.stack([idx, idx], axis=1), np.ones(int(n))
+    A = O.toarray() if sp.issparse(O) else np.asarray(O, dtype=np.float64)
+    i, j = np.triu_indices(A.shape[0])
+    v = A[i, j]
+    w = np.where(i == j, v, 2.0 * v)
+    keep = w != 0
+    return np.stack([i[keep], j[keep]], axis=1).astype(np.int64), w[keep]

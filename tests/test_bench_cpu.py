@@ -58,8 +58,8 @@ def test_roofline_picks_the_dominant_kernel_and_divides_by_its_peak():
     assert out["kernel"] == "force_tc" and out["bound"] == "tensor"
     achieved = 8.59e9 / 25e-6 / 1e12
     assert out["achieved"] == pytest.approx(achieved)
-    assert out["peak"] == pytest.approx(1678.5 * 1.1 / 2.25)
-    assert out["frac"] == pytest.approx(achieved / (1678.5 * 1.1 / 2.25))
+    assert out["peak"] == pytest.approx(1873.2 * 1.1 / 2.25)
+    assert out["frac"] == pytest.approx(achieved / (1873.2 * 1.1 / 2.25))
     assert out["share"] == {"force_tc": pytest.approx(2.5 / 4.5, abs=1e-4),
                             "gle_dense": pytest.approx(2.0 / 4.5, abs=1e-4)}
     prof = {"force_tc": (1.0, 100), "gle_dense": (2.0, 100)}
@@ -70,8 +70,9 @@ def test_roofline_picks_the_dominant_kernel_and_divides_by_its_peak():
 
 
 def test_sampled_exact_target_agrees_with_the_eigendecomposition():
-    """The lattice route (Chebyshev on a sample of elements) against U diag(g) U^T on a
-    lattice small enough for eigh: fed the exact expected values it reports zero error."""
+    """The lattice route (Chebyshev on a sample of elements, taken for orders beyond a
+    dense eigendecomposition) against U diag(g) U^T on a lattice small enough for eigh,
+    with a burn-in; fed the exact expected values the accuracy report shows zero error."""
     import numpy as np
     import fth_synth as syn
     from oracle import gle
@@ -85,7 +86,11 @@ def test_sampled_exact_target_agrees_with_the_eigendecomposition():
 
     class _Lattice:
         seed = 5
+        n = 10 ** 6                     # takes the sampled route
+        csr = (rowptr, col, val.astype(np.float32), 512)
         fit = {"kind": "fermi", "params": [2.0, 7.0]}
+        precision = "fp32"
+        trace = None
 
         def __init__(self):
             self.a_p, self.c_p, self.dt = a, c, dt
@@ -93,16 +98,25 @@ def test_sampled_exact_target_agrees_with_the_eigendecomposition():
         def oracle_matrix(self):
             return {"csr": (rowptr, col, val64, n)}
 
+    wl = _Lattice()
     pairs = np.concatenate([syn.diag_pairs(n), syn.lattice_nn_pairs(L)])
     lam, U = np.linalg.eigh(syn.csr_to_dense(rowptr, col, val64, n))
     T, S = gle.propagator(a, c, dt)
-    gm = gle.mode_response_mean(lam, T, S, dt, 0, 100)
-    GM = np.einsum("kj,kj->k", U[pairs[:, 0]] * gm[None, :], U[pairs[:, 1]])
-    out = bench.exact_target_sampled(_Lattice(), pairs, GM, np.full(len(pairs), 1e-3), 100, 1.0,
-                                     nsample=8, degree=300)
-    assert out["chebyshev_tail"] < 1e-10
-    assert out["rel_err"] < 1e-9
-    assert out["sigma_rel"] > 0 and out["steps_to_1e-3"] > 0
+    burnin, nacc = 7, 100
+    gm = gle.mode_response_mean(lam, T, S, dt, burnin, nacc)
+    GMall = np.einsum("kj,kj->k", U[pairs[:, 0]] * gm[None, :], U[pairs[:, 1]])
+    pick, G, GM, F, info, modes = bench._exact_values(wl, pairs, burnin, nacc, nsample=8,
+                                                      degree=300)
+    assert modes is None and len(pick) == 8
+    assert info["chebyshev_tail"] < 1e-10
+    assert np.allclose(GM, GMall[pick], rtol=1e-9, atol=1e-12)
+    acc = {"form": "fp32", "burnin": burnin, "block": 10, "accumulated": nacc, "tau_max": 3.0,
+           "snapshot": GMall, "trace": None,
+           "runs": {"fp32": {"vals": GMall, "errs": np.full(len(pairs), 1e-3),
+                             "ms_per_step": 1.0, "steps": burnin + nacc}}}
+    out = bench.exact_target(wl, pairs, acc)
+    assert out["fp32"]["rel_err"] < 1e-9
+    assert out["fp32"]["sigma_rel"] > 0 and out["fp32"]["steps_to_1e-3"] > burnin
 
 
 def test_ragged_exact_target_reports_zero_error_for_the_exact_values():
@@ -165,8 +179,8 @@ def test_serving_exact_scores_the_exact_values_at_zero():
         gm = gle.mode_response_mean(lam, T, S, 0.01, 0, 400)
         pr = r["pairs"]
         v = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
-        served[j] = (v, np.full(len(pr), 1e-3), 400)
-    served[3] = (np.zeros(4), np.ones(4), 400)          # a lattice request: not sampled
+        served[j] = (v, np.full(len(pr), 1e-3), 401)   # 401 pool steps: prologue + 400 samples
+    served[3] = (np.zeros(4), np.ones(4), 401)          # a lattice request: not sampled
     out = bench.serving_exact(wl, served, nsample=3)
     assert out["requests"] == 3 and out["elements"] == 96
     assert out["rel_err"] < 1e-12 and out["max_abs_z"] < 1e-6 and out["frac_abs_z_below_4"] == 1.0

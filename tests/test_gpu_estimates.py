@@ -92,6 +92,54 @@ def test_stationary_tf32_dense():
     assert 0.5 < np.mean(z ** 2) < 2.0
 
 
+# ------------------------------------------------------------------ calibrated error bars
+def _calibrated(a_p, c_p, dt, lo, hi):
+    """Burn-in 10 tau_max and blocks of max(1000, 10 tau_max) samples, tau_max the
+    library's correlation time of p^2 over [lo, hi] (fth_gle_response)."""
+    from paper_1402_2095_gb300 import binding
+    _, tau = binding.gle_response(a_p, c_p, dt, np.exp(np.linspace(np.log(lo), np.log(hi), 240)),
+                                  tau=True)
+    t = float(tau.max())
+    return int(np.ceil(10 * t)), max(1000, int(np.ceil(10 * t)))
+
+
+@pytest.mark.parametrize("kind", ["dense_tf32", "lattice_csr"])
+def test_calibrated_error_bars_at_a_fitted_gle(kind):
+    """With the stored Fermi fits (the benchmark's GLEs) and the calibrated burn-in and
+    block length, the block error bars describe the actual error against the exact
+    expected running mean: <z^2> within (0.5, 2) over every tracked element."""
+    from paper_1402_2095_gb300 import FTH, fit
+    nblocks = 20
+    if kind == "dense_tf32":
+        a, c, dt, rep = fit.load_gle("fermi_b5_dense4096")
+        M, _, _ = syn.dense_spd(384, 1.0, 1000.0, seed=1601)
+        Mo = M.astype(np.float32).astype(np.float64)
+        burnin, block = _calibrated(a, c, dt, 1.0, 1000.0)
+        pairs = syn.upper_pairs(384)
+        f = FTH(M=M.astype(np.float32), a_p=a, c_p=c, dt=dt, replicas=64, seed=1602,
+                precision="tf32", track="all", burnin=burnin, block=block)
+    else:
+        a, c, dt, rep = fit.load_gle("fermi_b2_lattice")
+        L = 7
+        rowptr, col, val = syn.lattice_csr(L, seed=1603)
+        v32 = val.astype(np.float32)
+        Mo = syn.csr_to_dense(rowptr, col, v32.astype(np.float64), L ** 3)
+        burnin, block = _calibrated(a, c, dt, 0.5, 14.5)
+        pairs = np.concatenate([syn.diag_pairs(L ** 3), syn.lattice_nn_pairs(L)])
+        f = FTH(csr=(rowptr, col, v32, L ** 3), a_p=a, c_p=c, dt=dt, replicas=64, seed=1604,
+                pairs=pairs, burnin=burnin, block=block)
+    f.run(burnin + nblocks * block)
+    assert f.info()["blocks"] == nblocks
+    vals, errs = f.elements(pairs)
+    T, S = gle.propagator(a, c, dt)
+    ref = matfun.g_mean_of_matrix(Mo, T, S, dt, burnin, nblocks * block)[pairs[:, 0], pairs[:, 1]]
+    z = (vals - ref) / errs
+    print(kind, "burnin", burnin, "block", block, "<z^2>", float(np.mean(z ** 2)))
+    assert 0.5 < np.mean(z ** 2) < 2.0
+    sample = np.random.default_rng(11).choice(len(pairs), 32, replace=False)
+    assert np.all(np.abs(z[sample]) < 5.0), z[sample]
+
+
 # ------------------------------------------------------------------ full size
 def test_full_size_dense_fp32_sampled():
     """N = 4096, R = 256 with the plain FP32 (FFMA) force: one fused step from a random

@@ -17,7 +17,7 @@ import fth_synth as syn
 from oracle import matfun
 from oracle.fth import fused_step_elements
 
-from gpu_util import gpu_ready, make_pair, state_rel_err
+from gpu_util import gpu_ready, make_pair, state_rel_err, trace_terms
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not gpu_ready(), reason="needs a CUDA GPU and libfth.so")]
@@ -340,7 +340,6 @@ def _functional_from_samples(samples, burnin, block, pairs, w):
 def test_functionals_csr_trace_and_trace_with_operator():
     """Tr f(M) and Tr M f(M) on a lattice (tracked: diagonal + nearest neighbours)."""
     import scipy.sparse as sp
-    from paper_1402_2095_gb300.binding import trace_terms
     L = 5
     n = L ** 3
     rowptr, col, val = syn.lattice_csr(L, seed=31)
@@ -350,7 +349,8 @@ def test_functionals_csr_trace_and_trace_with_operator():
                      seed=33, pairs=pairs, burnin=20, block=40)
     Mo = sp.csr_matrix((val.astype(np.float32).astype(np.float64), col, rowptr), shape=(n, n))
     terms = [trace_terms(n=n), trace_terms(O=Mo)]
-    ids = [g.add_functional(p, w) for p, w in terms]
+    # the library builds the weights itself (NULL operator: Tr f(M); a CSR operator)
+    ids = [g.add_trace(), g.add_trace(O=Mo)]
     g.run(420)
     samples = o.run(420, keep_samples=True)
     for fid, (p, w) in zip(ids, terms):
@@ -364,14 +364,13 @@ def test_functionals_csr_trace_and_trace_with_operator():
 
 
 def test_functional_fp64_dense_operator():
-    from paper_1402_2095_gb300.binding import trace_terms
     n = 12
     M = _dense(n)
     a, c = syn.random_gle(3, seed=34, rate=3.0)
     g, o = make_pair(M, a_p=a, c_p=c, dt=0.01, R=4, seed=35, precision="fp64", track="all",
                      burnin=0, block=25)
     p, w = trace_terms(O=M)
-    fid = g.add_functional(p, w)
+    fid = g.add_trace(O=M)                     # dense FP64 operator, weights built by the library
     g.run(250)
     samples = o.run(250, keep_samples=True)
     v, e = g.functional(fid)
@@ -383,15 +382,14 @@ def test_functional_fp64_dense_operator():
 def test_functional_dense_all_elements_tf32_tiles():
     """Functionals over the tile-packed all-elements accumulators of the tensor-core path
     (SYRK on the side stream, block fold before the flush)."""
-    from paper_1402_2095_gb300.binding import trace_terms
     n = 200
     M = _dense(n, seed=71)
     a, c = syn.random_gle(4, seed=72, rate=3.0)
     g, o = make_pair(M, a_p=a, c_p=c, dt=0.01, R=64, seed=73, precision="bf16x3", track="all",
                      burnin=10, block=30, M_oracle=M)
     p, w = trace_terms(O=M)
-    fid = g.add_functional(p, w)
-    tid = g.add_functional(*trace_terms(n=n))
+    fid = g.add_functional(p, w)               # explicit weights through fth_functional_add
+    tid = g.add_trace()
     g.run(310)
     samples = o.run(310, keep_samples=True)
     for f_id, (pp, ww) in ((fid, (p, w)), (tid, trace_terms(n=n))):
@@ -411,7 +409,6 @@ def test_trace_of_log_on_paper_m1_lattice():
     import scipy.sparse.linalg as spla
     from oracle import gle
     from paper_1402_2095_gb300 import FTH, fit, transforms
-    from paper_1402_2095_gb300.binding import trace_terms
     n1 = 7
     N = n1 ** 3
     rowptr, col, val = syn.m1_csr(n1, seed=91)
@@ -422,7 +419,7 @@ def test_trace_of_log_on_paper_m1_lattice():
     v32 = (r * val).astype(np.float32)
     g = FTH(csr=(rowptr, col, v32, N), a_p=a_p, c_p=c_p, dt=dt, replicas=64, seed=92,
             track="diag", block=500)
-    fid = g.add_functional(*trace_terms(n=N))
+    fid = g.add_trace()
     steps = 6000
     g.run(steps)
     tr_s, err_s = g.functional(fid)

@@ -100,21 +100,24 @@ def test_binary_is_sm103a_only(lib):
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
-def test_trace_terms_weights():
-    """sum_k w_k F_{i_k j_k} = Tr(O F) for symmetric O and F (dense and sparse O), and
-    the unit-weight form gives Tr F."""
-    import scipy.sparse as sp
-    from paper_1402_2095_gb300.binding import trace_terms
-    g = np.random.default_rng(5)
-    n = 9
-    A = g.standard_normal((n, n))
-    O = A + A.T
-    O[np.abs(O) < 0.5] = 0.0
-    B = g.standard_normal((n, n))
-    F = B + B.T
-    for op in (O, sp.csr_matrix(O)):
-        p, w = trace_terms(O=op)
-        assert np.isclose(np.sum(w * F[p[:, 0], p[:, 1]]), np.trace(O @ F))
-        assert np.all(p[:, 0] <= p[:, 1])
-    p, w = trace_terms(n=n)
-    assert np.isclose(np.sum(w * F[p[:, 0], p[:, 1]]), np.trace(F))
+def test_spectral_map_gle_scale_and_untransforms(lib):
+    """The C ABI's scaling / shift map and inverse transforms against their definitions."""
+    r, m = B.spectral_map((2.0, 10.0), (1.0, 601.0))
+    assert np.isclose(2.0 * r + m, 1.0) and np.isclose(10.0 * r + m, 601.0)
+    a, c = syn.random_gle(3, seed=8, rate=2.0)
+    a2, c2 = B.gle_scale(a, c, 0.5, 3.0)
+    assert np.array_equal(a2, 0.5 * a) and np.array_equal(c2, 3.0 * c)
+    pairs = np.array([[0, 0], [0, 1], [2, 2]])
+    v = np.array([1.0, 2.0, 3.0])
+    e = np.array([0.1, 0.2, 0.3])
+    lv, le = B.untransform("log", (4.0,), pairs, v, e)
+    assert np.allclose(lv, [1.0 - np.log(4.0), 2.0, 3.0 - np.log(4.0)]) and np.array_equal(le, e)
+    xv, xe = B.untransform("exp", (0.01, 301.0), pairs, v, e)
+    assert np.allclose(xv, v * np.exp(3.01)) and np.allclose(xe, e * np.exp(3.01))
+    pv, pe = B.untransform("power", (2.0, -0.5), pairs, v, e)
+    assert np.allclose(pv, v * np.sqrt(2.0)) and np.allclose(pe, e * np.sqrt(2.0))
+    assert np.isclose(B.untransform_trace("log", (4.0,), 10, 7.0), 7.0 - 10 * np.log(4.0))
+    with pytest.raises(B.FthError):
+        B.untransform("log", (-1.0,), pairs, v)
+    with pytest.raises(B.FthError):
+        B.spectral_map((1.0, 1.0), (0.0, 1.0))

@@ -177,3 +177,40 @@ def test_transient_mean_closed_form_equals_recursion(burnin, n):
         fast = gle.mode_response_mean(lams, T, S, 0.05, burnin, n, obs)
         slow = gle.mode_response_mean_recursive(lams, T, S, 0.05, burnin, n, obs)
         assert np.allclose(fast, slow, rtol=1e-9, atol=1e-12)
+
+
+def test_x2_correlation_time_predicts_the_variance_of_the_mean():
+    """The oracle's correlation time of p^2 against the FP64 integrator: for one mode
+    (N = 1, M = [lam]) and many independent replicas, the variance over replicas of the
+    time average of p^2 (after a burn-in) tends to 2 <p^2>^2 tau / n."""
+    from oracle.fth import OracleFTH
+    a, c = syn.random_gle(4, seed=21, rate=3.0)
+    dt, lam, R = 0.05, 2.0, 2000
+    T, S = gle.propagator(a, c, dt)
+    tau = gle.x2_correlation_time(lam, T, S, dt)
+    g = gle.discrete_cov(lam, T, S, dt)[1, 1]
+    assert 1.0 < tau < 500.0
+    nburn, n, chunk = int(20 * tau), int(400 * tau), 2000
+    o = OracleFTH(M=np.array([[lam]]), a_p=a, c_p=c, dt=dt, replicas=R, seed=5)
+    o.run(nburn)
+    acc = np.zeros(R)
+    done = 0
+    while done < n:
+        k = min(chunk, n - done)
+        x = o.run(k, keep_samples=True)[:, :, 0]
+        acc += np.sum(x * x, axis=0)
+        done += k
+    var = np.var(acc / n, ddof=1)
+    want = 2.0 * g * g * tau / n
+    # R = 2000 replicas: the sample variance is within ~3 % (1 sigma) of its mean; the
+    # finite length adds a relative O(tau / n) = 0.25 % bias
+    assert abs(var / want - 1.0) < 0.12, (var, want)
+
+
+def test_x2_correlation_time_white_noise_limit():
+    """s = 0 with a large friction: the O half-steps redraw p almost completely, so
+    successive end-of-step samples of p are nearly independent and tau -> 1."""
+    a, c = syn.white_noise_gle(2000.0, 1.0)
+    T, S = gle.propagator(a, c, 0.01)
+    tau = gle.x2_correlation_time(0.5, T, S, 0.01)
+    assert 1.0 <= tau < 1.01
