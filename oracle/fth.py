@@ -149,7 +149,7 @@ def fused_step_elements(M, q, p, s, T, S, dt, seed, kappa, elems, observable=0):
             mq = float((M.getrow(i) @ q[r])[0])
         else:
             mq = float(np.dot(M[i], q[r]))
-        zeta = native.normals(seed, kappa, i, r, ns + 1)
+        zeta = native.replica_normals(seed, kappa, i, r, ns + 1, ns + 1)
         v = np.concatenate([[p[r, i]], s[r, :, i]])
         qi = float(q[r, i])
         v[0] -= 0.5 * dt * mq

@@ -17,13 +17,16 @@
  *     (Sec. "Results and benchmarks", memory-footprint paragraph).
  *
  * Noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) written from its
- * published definition, and the Box-Muller transform.  For "kick index" kappa,
- * dof i and replica r, Philox call k uses counter (kappa, i, r, k) and key
- * (seed_lo, seed_hi).  Each uint32 pair (x0,x1) gives two normals:
+ * published definition, and the Box-Muller transform.  Replicas are paired: for
+ * "kick index" kappa, dof i and replica pair j, Philox call k uses counter
+ * (kappa, i, j, k) and key (seed_lo, seed_hi), and the calls k = 0, 1, ... form one
+ * stream of normals, four per call.  Each uint32 pair (x0,x1) gives two of them:
  *   u(x) = ((x >> 9) * 2 + 1) * 2^-24,  rho = sqrt(-2 ln u(x0)),
  *   n0 = rho cos(2 pi u(x1)),  n1 = rho sin(2 pi u(x1)).
- * The replica index in the counter is r + roff (roff: global index of the first
- * replica).
+ * Replica r (global index r + roff, roff: global index of the first replica) belongs
+ * to pair j = (r + roff) / 2 and takes the stream positions h W .. h W + W - 1,
+ * h = (r + roff) mod 2, W = ns + 1 (the normals one fused launch needs); so 2W normals
+ * per pair use all four words of ceil(2W / 4) calls.
  *
  * The two O half-steps of a fused launch (ending step kappa-1 and starting step
  * kappa) are separated only by the end-of-step sample, which observes p after the
@@ -96,6 +99,18 @@ void oracle_normals(uint64_t seed, uint32_t kappa, uint32_t i, uint32_t r, int c
     }
 }
 
+/* The first `count` (<= width) normals of global replica r: stream positions
+ * (r mod 2) * width + t of the pair stream of j = r / 2. */
+void oracle_replica_normals(uint64_t seed, uint32_t kappa, uint32_t i, uint32_t r, int width,
+                            int count, double* out)
+{
+    double buf[4 * ((2 * (NS_MAX + 1) + 3) / 4)];
+    const int need = 4 * ((2 * width + 3) / 4);
+    oracle_normals(seed, kappa, i, r >> 1, need, buf);
+    const int h0 = (int)(r & 1u) * width;
+    for (int t = 0; t < count; ++t) out[t] = buf[h0 + t];
+}
+
 /* ---------------------------------------------------------------- force */
 /* F[r][i] = -(M q_r)_i.  kind 0: dense row-major n x n; kind 1: CSR. */
 static void force(int64_t n, int64_t R, int kind, const double* Md, const int64_t* rowptr,
@@ -157,7 +172,7 @@ int oracle_prologue(int64_t n, int64_t R, int ns, int kind, const double* Md,
     for (int64_t r = 0; r < R; ++r) {
         double xi[2 * NS_MAX], v[NS_MAX];
         for (int64_t i = 0; i < n; ++i) {
-            oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, ns, xi);
+            oracle_replica_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, ns + 1, ns, xi);
             load_v(n, ns, r, i, p, s, v);
             o_half(ns, T, S, v, xi);
             v[0] += 0.5 * dt * F[r * n + i];
@@ -211,7 +226,7 @@ int oracle_steps(int64_t n, int64_t R, int ns, int kind, const double* Md,
             const int m = ns + 1;
             for (int64_t i = 0; i < n; ++i) {
                 const double f = F[r * n + i];
-                oracle_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, m, zeta);
+                oracle_replica_normals(seed, kappa, (uint32_t)i, (uint32_t)r + roff, m, m, zeta);
                 load_v(n, ns, r, i, p, s, v);
                 v[0] += 0.5 * dt * f;          /* B(dt/2), end of the current step */
                 /* p after the end-of-step O(dt/2): (T v)_0 + x, x = (L zeta)_0 */

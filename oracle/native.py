@@ -50,6 +50,8 @@ def _declare(L):
     L.oracle_philox4x32_10.restype = None
     L.oracle_normals.argtypes = [U64, U32, U32, U32, INT, P]
     L.oracle_normals.restype = None
+    L.oracle_replica_normals.argtypes = [U64, U32, U32, U32, INT, INT, P]
+    L.oracle_replica_normals.restype = None
     L.oracle_prologue.argtypes = [I64, I64, INT, INT, P, P, P, P, P, P, D, U64, U32, U32, P, P, P]
     L.oracle_prologue.restype = INT
     L.oracle_steps.argtypes = ([I64, I64, INT, INT, P, P, P, P, P, P, P, P, D, U64, U32, U32, I64, P,
@@ -73,7 +75,18 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def normals(seed: int, kappa: int, i: int, r: int, count: int) -> np.ndarray:
+def normals(seed: int, kappa: int, i: int, j: int, count: int) -> np.ndarray:
+    """The first `count` normals of the stream of counter word j (a replica pair):
+    Philox calls k = 0, 1, ... with counter (kappa, i, j, k), four normals per call."""
     out = np.zeros(((count + 3) // 4) * 4, dtype=np.float64)
-    lib().oracle_normals(U64(seed), U32(kappa), U32(i), U32(r), INT(count), ptr(out))
+    lib().oracle_normals(U64(seed), U32(kappa), U32(i), U32(j), INT(count), ptr(out))
     return out[:count]
+
+
+def replica_normals(seed: int, kappa: int, i: int, r: int, width: int, count: int) -> np.ndarray:
+    """The first `count` of the `width` normals of global replica r: positions
+    (r mod 2) * width + t of the stream of its pair r // 2."""
+    out = np.zeros(count, dtype=np.float64)
+    lib().oracle_replica_normals(U64(seed), U32(kappa), U32(i), U32(r), INT(width), INT(count),
+                                 ptr(out))
+    return out

@@ -86,7 +86,8 @@ def _python_integrator(Mfull, T, S, dt, seed, R, steps):
     f = F(q)
     for r in range(R):
         for i in range(n):
-            xi = native.normals(seed, 0, i, r, ns)
+            # replica r takes positions (r % 2) (ns + 1) .. of the stream of pair r // 2
+            xi = native.normals(seed, 0, i, r // 2, 2 * (ns + 1))[(r % 2) * (ns + 1):][:ns]
             v[r, i] = O(v[r, i], xi)
             v[r, i, 0] += 0.5 * dt * f[r, i]
             q[r, i] += dt * v[r, i, 0]
@@ -96,7 +97,7 @@ def _python_integrator(Mfull, T, S, dt, seed, R, steps):
         X = np.zeros((R, n))
         for r in range(R):
             for i in range(n):
-                zeta = native.normals(seed, t, i, r, ns + 1)
+                zeta = native.normals(seed, t, i, r // 2, 2 * (ns + 1))[(r % 2) * (ns + 1):][:ns + 1]
                 xy = [sum(Lj[a, b] * zeta[b] for b in range(a + 1)) for a in range(ns + 1)]
                 v[r, i, 0] += 0.5 * dt * f[r, i]
                 X[r, i] = sum(T[0, b] * v[r, i, b] for b in range(ns)) + xy[0]

@@ -79,3 +79,29 @@ def test_uniform_map_is_open_interval():
     lo = ((0 >> 9) * 2 + 1) / 2.0 ** 24
     hi = (((2 ** 32 - 1) >> 9) * 2 + 1) / 2.0 ** 24
     assert lo == 2.0 ** -24 and hi == 1 - 2.0 ** -24
+
+
+def test_replica_normals_take_their_half_of_the_pair_stream():
+    """Replicas 2j and 2j + 1 share the stream of counter word j: the even one takes
+    positions 0..W-1, the odd one W..2W-1; all four words of every call are used."""
+    seed, kappa, i, W = 99, 5, 17, 6
+    for j in (0, 3, 1000):
+        raw = native.normals(seed, kappa, i, j, 12)
+        assert np.array_equal(native.replica_normals(seed, kappa, i, 2 * j, W, W), raw[:W])
+        assert np.array_equal(native.replica_normals(seed, kappa, i, 2 * j + 1, W, W), raw[W:])
+        # the prologue's first W - 1 of the same slot
+        assert np.array_equal(native.replica_normals(seed, kappa, i, 2 * j + 1, W, W - 1),
+                              raw[W:2 * W - 1])
+    # odd width: the second replica starts mid-call
+    raw = native.normals(seed, kappa, i, 7, 12)
+    assert np.array_equal(native.replica_normals(seed, kappa, i, 15, 5, 5), raw[5:10])
+
+
+def test_replica_pair_normals_are_uncorrelated():
+    n = 40000
+    a = np.array([native.replica_normals(3, k, k % 31, 2 * (k % 17), 6, 6) for k in range(n)])
+    b = np.array([native.replica_normals(3, k, k % 31, 2 * (k % 17) + 1, 6, 6) for k in range(n)])
+    c = np.corrcoef(np.concatenate([a, b], axis=1).T)
+    off = c[~np.eye(12, dtype=bool)]
+    assert np.max(np.abs(off)) < 5 / np.sqrt(n)
+    assert abs(np.mean(np.concatenate([a, b]) ** 2) - 1.0) < 5 * np.sqrt(2.0 / (12 * n))
