@@ -534,6 +534,7 @@ class Ragged:
         self.seed = syn.BASE_SEED + 3
         self.sizes = syn.ragged_sizes(self.count, seed=self.seed)
         self.a_p, self.c_p, self.dt, self.fit = fit.load_gle("inv_sqrt_1_100")
+        self.block = calibrated_blocks(self.a_p, self.c_p, self.dt, self.fit["lam"])[2]
         self.mats, self.pairs = [], []
         for k, n in enumerate(self.sizes):
             M, _, _ = syn.dense_spd(int(n), 1.0, 100.0, seed=self.seed * 1000 + k)
@@ -651,21 +652,38 @@ def run_ragged(args, rank, world, local):
         "e2e": {"value": wl.count * wl.R * steps * world / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps},
     }
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        # fixed-length pass with calibrated burn-in and blocks (independent of --steps)
+        tau, burnin, block = calibrated_blocks(wl.a_p, wl.c_p, wl.dt, wl.fit["lam"])
+        nblocks = args.accuracy_blocks
+        pa = Pool(ws, replicas=wl.R, precision="bf16x3", max_problems=wl.count,
+                  graph_steps=wl.graph_steps)
+        hs = [pa.add(**dict(wl.problem(k, seed_shift=2), burnin=burnin, block=block))
+              for k in range(wl.count)]
+        nsteps = 1 + burnin + nblocks * block          # the first pool step is the prologue
+        pa.run(nsteps)
+        acc_read = {k: pa.elements(hs[k], wl.pairs[k]) for k in range(wl.count)}
+        pa.close()
+        line["accuracy"] = {"form": "bf16x3", "tau_max": tau, "burnin": burnin, "block": block,
+                            "blocks": nblocks, "accumulated": nblocks * block, "steps": nsteps}
+        if not args.no_cpu_baseline:
+            line["accuracy"]["exact"] = exact_target_ragged(wl, acc_read, burnin,
+                                                            nblocks * block, ms / steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ragged(wl)
-        line["cpu_baseline"]["exact"] = exact_target_ragged(wl, read, steps, ms / steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
-def exact_target_ragged(wl, read, steps, ms_per_step, nsample=8):
+def exact_target_ragged(wl, read, burnin, nacc, ms_per_step, nsample=8):
     """exact_target for the pool: on a seeded sample of problems, each problem's exact
-    values by the oracle's eigendecomposition (g, the expected running mean after `steps`
-    samples, f) at its tracked pairs, against the values and error bars the end-to-end
-    pool returned (`read[k]` = (values, errbars) of problem k).  Norms over the sample's
-    elements together; all problems advance one step per pool step, so the time to 1e-3
-    is in pool steps."""
+    values by the oracle's eigendecomposition (g, the expected running mean after `burnin`
+    discarded and `nacc` accumulated samples, f) at its tracked pairs, against the values
+    and error bars the pool returned (`read[k]` = (values, errbars) of problem k).  Norms
+    over the sample's elements together; all problems advance one step per pool step, so
+    the time to 1e-3 is in pool steps: burn-in + nacc (sigma_rel / 1e-3)^2."""
+    steps = nacc
     from oracle import gle, matfun
     t0 = time.perf_counter()
     pick = np.random.default_rng(wl.seed + 1).choice(wl.count, size=nsample, replace=False)
@@ -678,7 +696,7 @@ def exact_target_ragged(wl, read, steps, ms_per_step, nsample=8):
         pr = wl.pairs[k]
         a, b = U[pr[:, 0]], U[pr[:, 1]]
         for out, d in ((G, gle.mode_response(lam, T, S, wl.dt)),
-                       (GM, gle.mode_response_mean(lam, T, S, wl.dt, 0, steps)),
+                       (GM, gle.mode_response_mean(lam, T, S, wl.dt, burnin, nacc)),
                        (F, matfun.f_scalar(fk, lam, fp))):
             out.append(np.einsum("kj,kj->k", a * d[None, :], b))
         V.append(read[k][0])
@@ -688,11 +706,14 @@ def exact_target_ragged(wl, read, steps, ms_per_step, nsample=8):
     ng = float(np.linalg.norm(G))
     sig = float(np.linalg.norm(E)) / ng
     sig_d = float(np.linalg.norm(E[D]) / np.linalg.norm(G[D]))
-    t_all, t_d = steps * (sig / 1e-3) ** 2, steps * (sig_d / 1e-3) ** 2
+    t_all = burnin + steps * (sig / 1e-3) ** 2
+    t_d = burnin + steps * (sig_d / 1e-3) ** 2
+    z = (V - GM) / E
     return {
         "sample": f"{nsample} of {wl.count} problems (seeded), {len(G)} tracked elements",
-        "eigh_s": time.perf_counter() - t0, "steps": steps,
+        "eigh_s": time.perf_counter() - t0, "burnin": burnin, "accumulated": nacc,
         "rel_err": float(np.linalg.norm(V - GM)) / ng, "sigma_rel": sig,
+        "z2": float(np.mean(z * z)),
         "transient": float(np.linalg.norm(GM - G)) / ng,
         "fit_bias": float(np.linalg.norm(G - F) / np.linalg.norm(F)),
         "time_to_1e-3_s": t_all * ms_per_step / 1e3, "steps_to_1e-3": t_all,
@@ -739,7 +760,7 @@ class Serving:
 
     name = "serving"
 
-    def __init__(self, rate=200.0, window=1.0, t_hi=0.1, t_lo=0.03, budget=10000, distinct=8):
+    def __init__(self, rate=200.0, window=1.0, t_hi=0.1, t_lo=0.03, budget=40000, distinct=8):
         from paper_1402_2095_gb300 import fit
         self.seed = syn.BASE_SEED + 4
         g = np.random.default_rng(self.seed)
@@ -747,6 +768,9 @@ class Serving:
         self.arrivals = syn.poisson_arrivals(rate, window, seed=self.seed)
         self.fits = {k: fit.load_gle(k) for k in ("inv_sqrt_1_100", "fermi_b2_1_100",
                                                    "inv_sqrt_lattice", "fermi_b2_lattice")}
+        # blocks calibrated per fit (correlation time of p^2 over its range)
+        self.blocks = {k: calibrated_blocks(a, c, dt, rep["lam"])[2]
+                       for k, (a, c, dt, rep) in self.fits.items()}
         self.dense, self.lattice = [], []
         for k in range(distinct):
             n = int(g.integers(128, 4097))
@@ -779,12 +803,14 @@ class Serving:
                     lattice_inv_sqrt.append(j)
             a_p, c_p, dt, _ = self.fits[fname]
             self.reqs.append(dict(mat, a_p=a_p, c_p=c_p, dt=dt, seed=self.seed * 10000 + j,
-                                  block=1000, pairs=pairs, target=target, max_steps=budget))
+                                  block=self.blocks[fname], pairs=pairs, target=target,
+                                  max_steps=budget))
         self.lattice_inv_sqrt = lattice_inv_sqrt
         self.label = (f"Poisson {rate:g} req/s over {window:g} s ({len(self.reqs)} requests); 50% "
                       f"dense N~U[128,4096] / 50% lattice L~U{{16..48}}; f in {{x^-1/2, Fermi b=2}}; "
-                      f"targets {t_hi:g}/{t_lo:g} (normwise rel. error bar), budget {budget} "
-                      f"steps; 32 elements; R=32 each")
+                      f"targets {t_hi:g}/{t_lo:g} (normwise rel. error bar over blocks of "
+                      f"max(1000, 10 tau_max) samples), budget {budget} steps; 32 elements; "
+                      f"R=32 each")
 
 
 def run_serving(args, rank, world, local):
@@ -853,6 +879,7 @@ def run_serving(args, rank, world, local):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/f32",
         "data": "synthetic",
         "config": {"workload": wl.label, "requests": len(wl.reqs), "submitted": len(ids),
+                   "blocks": wl.blocks,
                    "states": states, "chunk_steps": 1000, "min_blocks": 4,
                    "workspace_gb": args.serve_gb, "peak_used_gb": peak_used / 2 ** 30,
                    "l2": "resident working set of all admitted requests >> L2"},
@@ -986,7 +1013,7 @@ def main():
                              "m2"])
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--window", type=float, default=1.0, help="serving: arrival window (s)")
-    ap.add_argument("--budget", type=int, default=10000, help="serving: step budget per request")
+    ap.add_argument("--budget", type=int, default=40000, help="serving: step budget per request")
     ap.add_argument("--serve-gb", type=int, default=64, help="serving: pool workspace (GiB)")
     ap.add_argument("--serve-timeout", type=float, default=300.0, help="serving: wall limit (s)")
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16x3"])

@@ -146,7 +146,7 @@ def test_ragged_exact_target_reports_zero_error_for_the_exact_values():
         pr = wl.pairs[k]
         v = np.einsum("kj,kj->k", U[pr[:, 0]] * gm[None, :], U[pr[:, 1]])
         read[k] = (v, np.full(len(pr), 1e-3))
-    out = bench.exact_target_ragged(wl, read, 300, 0.25, nsample=2)
+    out = bench.exact_target_ragged(wl, read, 0, 300, 0.25, nsample=2)
     assert out["rel_err"] < 1e-12
     assert out["sigma_rel"] > 0 and out["time_to_1e-3_s"] > 0 and out["fit_bias"] > 0
 
