@@ -2,13 +2,16 @@
 //
 // Noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
 // multiply-xor S-box on a 4x32-bit counter with a 2x32-bit key bumped by the Weyl
-// constants between rounds.  For kick index kappa, dof i, replica r, call k uses
-// counter (kappa, i, r, k) and key (seed_lo, seed_hi).  Box-Muller turns each uint32
-// pair (a, b) into two normals rho*cos(2 pi u_b), rho*sin(2 pi u_b) with
-// rho = sqrt(-2 ln u_a) and u(x) = ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and
-// never 0 or 1.  A fused launch (end of step kappa-1 and start of step kappa) uses
-// normals 0..ns of kappa for its two O half-steps, drawn jointly (gle_fused); a launch
-// with one half-step (the prologue) uses normals 0..ns-1.
+// constants between rounds.  Replicas are paired: for kick index kappa, dof i and pair
+// j, call k uses counter (kappa, i, j, k) and key (seed_lo, seed_hi), and the calls
+// form one stream of normals, four per call.  Box-Muller turns each uint32 pair (a, b)
+// into two normals rho*cos(2 pi u_b), rho*sin(2 pi u_b) with rho = sqrt(-2 ln u_a) and
+// u(x) = ((x >> 9) * 2 + 1) * 2^-24, exact in FP32 and never 0 or 1.  Global replica g
+// (index plus the replica offset) belongs to pair g / 2 and takes stream positions
+// (g mod 2) W .. (g mod 2) W + W - 1, W = ns + 1.  A fused launch (end of step kappa-1
+// and start of step kappa) uses those W normals of kappa for its two O half-steps,
+// drawn jointly (gle_fused); a launch with one half-step (the prologue) uses the first
+// ns of them.
 #pragma once
 
 #include <stdint.h>
@@ -63,21 +66,69 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
     z1 = -rho * sn;
 }
 
-// The NS + 1 normals of (kappa, i, r) a fused launch needs.
+// The W = NS + 1 normals of both replicas of pair j (global replicas 2j and 2j + 1):
+// all four words of each of the ceil(2W / 4) calls.
 template <int NS>
-__device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t r,
-                                            const uint32_t* rk, float (&xi)[NS + 1]) {
-    constexpr int kCount = NS + 1;
-    constexpr int kCalls = (kCount + 3) / 4;
+__device__ __forceinline__ void gle_normals_pair(uint32_t kappa, uint32_t i, uint32_t j,
+                                                 const uint32_t* rk, float (&xa)[NS + 1],
+                                                 float (&xb)[NS + 1]) {
+    constexpr int W = NS + 1;
+    constexpr int kCalls = (2 * W + 3) / 4;
 #pragma unroll
     for (int k = 0; k < kCalls; ++k) {
-        const uint4 x = philox4x32_10_rk(make_uint4(kappa, i, r, (uint32_t)k), rk);
+        const uint4 x = philox4x32_10_rk(make_uint4(kappa, i, j, (uint32_t)k), rk);
         float z[4];
         box_muller(x.x, x.y, z[0], z[1]);
-        if (4 * k + 2 < kCount) box_muller(x.z, x.w, z[2], z[3]);
+        if (4 * k + 2 < 2 * W) box_muller(x.z, x.w, z[2], z[3]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (4 * k + j < kCount) xi[4 * k + j] = z[j];
+        for (int t = 0; t < 4; ++t) {
+            const int pos = 4 * k + t;
+            if (pos < W) xa[pos] = z[t];
+            else if (pos < 2 * W) xb[pos - W] = z[t];
+        }
+    }
+}
+
+// Half H (0: even replica, 1: odd) of pair j alone: only the calls and Box-Muller
+// transforms that cover stream positions H W .. H W + W - 1.
+template <int NS, int H>
+__device__ __forceinline__ void gle_normals_half(uint32_t kappa, uint32_t i, uint32_t j,
+                                                 const uint32_t* rk, float (&xi)[NS + 1]) {
+    constexpr int W = NS + 1;
+    constexpr int p0 = H * W, p1 = H * W + W;     // [p0, p1)
+#pragma unroll
+    for (int k = p0 / 4; k <= (p1 - 1) / 4; ++k) {
+        const uint4 x = philox4x32_10_rk(make_uint4(kappa, i, j, (uint32_t)k), rk);
+        float z[4];
+        if (4 * k + 2 > p0 && 4 * k < p1) box_muller(x.x, x.y, z[0], z[1]);
+        if (4 * k + 4 > p0 && 4 * k + 2 < p1) box_muller(x.z, x.w, z[2], z[3]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int pos = 4 * k + t;
+            if (pos >= p0 && pos < p1) xi[pos - p0] = z[t];
+        }
+    }
+}
+
+// The NS + 1 normals of one global replica g alone.
+template <int NS>
+__device__ __forceinline__ void gle_normals(uint32_t kappa, uint32_t i, uint32_t g,
+                                            const uint32_t* rk, float (&xi)[NS + 1]) {
+    if (g & 1u) gle_normals_half<NS, 1>(kappa, i, g >> 1, rk, xi);
+    else gle_normals_half<NS, 0>(kappa, i, g >> 1, rk, xi);
+}
+
+// The normals of two consecutive global replicas g and g + 1: one pair stream when they
+// form a pair (g even), else each alone.
+template <int NS>
+__device__ __forceinline__ void gle_normals_two(uint32_t kappa, uint32_t i, uint32_t g,
+                                                const uint32_t* rk, float (&xa)[NS + 1],
+                                                float (&xb)[NS + 1]) {
+    if ((g & 1u) == 0u) {
+        gle_normals_pair<NS>(kappa, i, g >> 1, rk, xa, xb);
+    } else {
+        gle_normals_half<NS, 1>(kappa, i, g >> 1, rk, xa);
+        gle_normals_half<NS, 0>(kappa, i, (g >> 1) + 1u, rk, xb);
     }
 }
 

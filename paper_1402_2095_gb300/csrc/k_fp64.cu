@@ -30,34 +30,43 @@ __device__ __forceinline__ void box_muller64(uint32_t a, uint32_t b, double& z0,
 // Noise ahead of the integrator: the NS + 1 normals of every (kappa, i, r) of a segment
 // of `iters` kick indices from kappa0, written to xi[((it R + r) (NS + 1) + a) Np + i]
 // (a fused launch draws its two O half-steps jointly from NS + 1 normals; the prologue
-// uses the first NS).  FP64
-// transcendental functions are the bulk of the FP64 path's work; this kernel spreads
+// uses the first NS).  Replicas share streams in pairs (gle_device.cuh): global replica
+// g = r + roff takes positions (g mod 2) W .. of the stream of pair g / 2, W = NS + 1.
+// FP64 transcendental functions are the bulk of the FP64 path's work; this kernel spreads
 // them over the whole GPU while the integrator (one CTA per replica) stays small.
-// One thread per (it, r, Philox call k, i), i fastest, so the stores coalesce.
+// One thread per (it, pair, Philox call k, i), i fastest, so the stores coalesce; each
+// call's four normals go to whichever of the pair's replicas are in this run.
 template <int NS>
 __global__ void __launch_bounds__(256)
 fp64_noise_kernel(uint32_t key0, uint32_t key1, uint32_t roff, int N, int Np, int R,
                   uint32_t kappa0, int iters, double* __restrict__ xi) {
-    constexpr int kCount = NS + 1;
-    constexpr int kCalls = (kCount + 3) / 4;
-    const int64_t total = (int64_t)iters * R * kCalls * N;
+    constexpr int W = NS + 1;
+    constexpr int kCalls = (2 * W + 3) / 4;
+    const uint32_t j0 = roff >> 1;                           // first pair of this run
+    const int npairs = (int)(((roff + (uint32_t)R - 1u) >> 1) - j0 + 1u);
+    const int64_t total = (int64_t)iters * npairs * kCalls * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % N);
         int64_t rest = e / N;
         const int k = (int)(rest % kCalls);
         rest /= kCalls;
-        const int r = (int)(rest % R);
-        const int it = (int)(rest / R);
-        const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i,
-                                                 (uint32_t)r + roff, (uint32_t)k), key0, key1);
-        double* out = xi + ((int64_t)it * R + r) * kCount * Np + i;
+        const uint32_t j = j0 + (uint32_t)(rest % npairs);
+        const int it = (int)(rest / npairs);
+        const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i, j,
+                                                 (uint32_t)k), key0, key1);
         double z[4];
         box_muller64(x.x, x.y, z[0], z[1]);
-        if (4 * k + 2 < kCount) box_muller64(x.z, x.w, z[2], z[3]);
+        if (4 * k + 2 < 2 * W) box_muller64(x.z, x.w, z[2], z[3]);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (4 * k + j < kCount) out[(int64_t)(4 * k + j) * Np] = z[j];
+        for (int t = 0; t < 4; ++t) {
+            const int pos = 4 * k + t;
+            if (pos >= 2 * W) continue;
+            const int h = pos >= W ? 1 : 0;
+            const int64_t r = (int64_t)(2u * j + (uint32_t)h) - (int64_t)roff;   // local replica
+            if (r < 0 || r >= R) continue;
+            xi[(((int64_t)it * R + r) * W + (pos - h * W)) * Np + i] = z[t];
+        }
     }
 }
 
@@ -315,8 +324,8 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
                               uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st) {
     if (iters <= 0) return cudaSuccess;
-    const int64_t calls = (ns + 1 + 3) / 4;
-    const int64_t total = iters * R * calls * N;
+    const int64_t calls = (2 * (ns + 1) + 3) / 4;                  // per replica pair
+    const int64_t total = iters * (R / 2 + 1) * calls * N;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
 #define FTH_F64N_CASE(NSV)                                                                  \
     case NSV:                                                                               \

@@ -336,18 +336,37 @@ __device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, const GleF3
     const float* mqa = reinterpret_cast<const float*>(&mq4);
     V sv;
     float* samp = reinterpret_cast<float*>(&sv);
-#pragma unroll
-    for (int e = 0; e < NE; ++e) {
+    if constexpr (NE == 1) {
         float v[NS];
 #pragma unroll
-        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
+        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[0];
         float xi[NS + 1];
-        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xi);
-        samp[e] = 0.f;
-        gle_fused<NS>(qa[e], v, mqa[e], gk, xi, c.flags, c.observable, samp[e]);
+        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)r0 + c.roff, c.rk, xi);
+        samp[0] = 0.f;
+        gle_fused<NS>(qa[0], v, mqa[0], gk, xi, c.flags, c.observable, samp[0]);
 #pragma unroll
-        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
-        qout[e] = qa[e];
+        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[0] = v[a];
+        qout[0] = qa[0];
+    } else {
+        // replicas two at a time: one pair stream of normals serves both
+#pragma unroll
+        for (int e = 0; e < NE; e += 2) {
+            float xa[NS + 1], xb[NS + 1];
+            gle_normals_two<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xa, xb);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ee = e + h;
+                float v[NS];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[ee];
+                samp[ee] = 0.f;
+                if (h == 0) gle_fused<NS>(qa[ee], v, mqa[ee], gk, xa, c.flags, c.observable, samp[ee]);
+                else gle_fused<NS>(qa[ee], v, mqa[ee], gk, xb, c.flags, c.observable, samp[ee]);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[ee] = v[a];
+                qout[ee] = qa[ee];
+            }
+        }
     }
     *reinterpret_cast<V*>(c.q + off) = q4;
     *reinterpret_cast<V*>(c.p + off) = v4[0];
@@ -519,16 +538,22 @@ __device__ __forceinline__ void pool_csr_quad(const PoolCsrShared& c, const GleF
     float* qa = reinterpret_cast<float*>(&q4);
     const float* mqa = reinterpret_cast<const float*>(&mq4);
     float samp[4] = {0.f, 0.f, 0.f, 0.f};
+    // replicas two at a time: one pair stream of normals serves both
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float v[NS];
+    for (int e = 0; e < 4; e += 2) {
+        float xa[NS + 1], xb[NS + 1];
+        gle_normals_two<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xa, xb);
 #pragma unroll
-        for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[e];
-        float xi[NS + 1];
-        gle_normals<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xi);
-        gle_fused<NS>(qa[e], v, mqa[e], gk, xi, c.flags, c.observable, samp[e]);
+        for (int h = 0; h < 2; ++h) {
+            const int ee = e + h;
+            float v[NS];
 #pragma unroll
-        for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[e] = v[a];
+            for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[ee];
+            if (h == 0) gle_fused<NS>(qa[ee], v, mqa[ee], gk, xa, c.flags, c.observable, samp[ee]);
+            else gle_fused<NS>(qa[ee], v, mqa[ee], gk, xb, c.flags, c.observable, samp[ee]);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[ee] = v[a];
+        }
     }
     *reinterpret_cast<float4*>(c.qout + off) = q4;
     *reinterpret_cast<float4*>(c.p + off) = v4[0];
