@@ -30,11 +30,11 @@ FITS = {
     "fermi_b2_lattice": ("fermi", (2.0, 7.0), 0.5, 14.5, dict(starts=8, max_iter=1500)),
     # request mix of the serving loop: the two functions on both spectral ranges
     "fermi_b2_1_100": ("fermi", (2.0, 10.0), 1.0, 100.0, dict(starts=8, max_iter=1500)),
-    "inv_sqrt_lattice": ("inv_sqrt", (), 0.5, 14.5, dict(starts=8, max_iter=1500)),
+    "inv_sqrt_lattice": ("inv_sqrt", (), 0.5, 14.5, dict(starts=16, max_iter=3000)),
     # the paper's two benchmark functions: ln on [e, 100 e] (M1 scaled into it, then
     # ln M = ln(rM) - I ln r) and exp(-x/100) on [1, 601] (M2 + 301 I, eigenvalues of M2
     # in (-300, 300); exp(-M2/100) = exp(-(M2 + 301 I)/100) e^3.01)
-    "log_e_100e": ("log", (), float(np.e), float(100 * np.e), dict(starts=8, max_iter=1500)),
+    "log_e_100e": ("log", (), float(np.e), float(100 * np.e), dict(starts=32, max_iter=3000)),
     "exp_001_1_601": ("exp", (0.01,), 1.0, 601.0, dict(starts=8, max_iter=1500)),
 }
 
