@@ -621,6 +621,9 @@ fth_status flush(fth_ctx* c) {
 // The force arrives as one plane (the split-K kernel reduces its K shares on chip).
 int mq_planes(const fth_ctx*) { return 1; }
 
+// kZeroMQ when the force adds its partial sums into MQ (the element-wise step zeroes it).
+int zero_mq(const fth_ctx* c) { return c->tcf && tc_force_accumulates(c->tcf) ? kZeroMQ : 0; }
+
 void op_ptrs(fth_ctx* c, int& kind, void*& hi, void*& lo) {
     kind = kOpNone;
     hi = lo = nullptr;
@@ -645,8 +648,8 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
         {
             ProfScope ps(c, FTH_K_GLE_DENSE);
             FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, mq_planes(c), q, p, s,
-                                    (uint32_t)c->t, kDoStart, c->observable, c->ps, L.ps_ld, 0,
-                                    opk, hi, lo, L.Np, c->stream),
+                                    (uint32_t)c->t, kDoStart | zero_mq(c), c->observable, c->ps,
+                                    L.ps_ld, 0, opk, hi, lo, L.Np, c->stream),
                    "gle prologue");
         }
         ++c->launches;
@@ -660,7 +663,7 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
         // the tcgen05 accumulation pass reads the samples as TF32: round them to nearest
         const bool tf32_samples = is_tc(c) && L.track == FTH_TRACK_ALL;
         const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0) |
-                          (take && tf32_samples ? kSampleTf32 : 0);
+                          (take && tf32_samples ? kSampleTf32 : 0) | zero_mq(c);
         if (take && c->nfill == 0) {
             st = claim_stack(c);
             if (st != FTH_OK) return st;
@@ -1090,7 +1093,8 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     // ---- tensor maps
     if (is_tc(c)) {
         const int kind = L.precision == FTH_PREC_TF32 ? 1 : 2;
-        FTH_CK_C(tc_force_prepare(&c->tcf, kind, c->M, c->Mlo, c->ophi, c->oplo, L.Np, L.Rp, L.N, L.R),
+        FTH_CK_C(tc_force_prepare(&c->tcf, kind, c->M, c->Mlo, c->ophi, c->oplo, L.Np, L.Rp, L.N, L.R,
+                                  c->MQ),
                  "tensor maps (force)");
         if (L.track == FTH_TRACK_ALL) {
             FTH_CK_C(tc_syrk_prepare(&c->tcs, c->psb[0], L.Np, L.ps_ld), "tensor maps (syrk)");

@@ -69,8 +69,9 @@ cudaError_t launch_dense_prepare(const void* src, int f64, int64_t n, int64_t r0
 // Flags of the dense element-wise GLE kernel.  kSampleTf32: stage the samples rounded
 // to TF32 (round to nearest), because the tensor-core accumulation pass reads them as
 // kind::tf32 operands and the MMA drops the low 13 mantissa bits (truncation, a bias of
-// ~7e-4 per product otherwise).
-enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleTf32 = 8 };
+// ~7e-4 per product otherwise).  kZeroMQ: write zeros over MQ after reading it (the force
+// adds its partial sums into MQ).
+enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleTf32 = 8, kZeroMQ = 16 };
 
 // Operand copies of q the element-wise kernel writes for the force GEMM.
 enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
@@ -78,7 +79,7 @@ enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
 // ------------------------------------------------------------------ kernels
 // Dense path, state planes [Np][Rp] FP32 (replica fastest), MQ = M q (positive).
 cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
-                             const float* MQ, int mq_planes, float* q, float* p, float* s,
+                             float* MQ, int mq_planes, float* q, float* p, float* s,
                              uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
@@ -152,15 +153,18 @@ cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, in
 
 // tcgen05 / TMA kernels (sm_103a).
 struct TcForce;   // opaque, holds the tensor maps
+// MQ (may be NULL): the [Np][Rp] output, for the row-pair kernel's reduce-add map.
 cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const void* A_lo,
                              const void* B_hi, const void* B_lo, int64_t Np, int64_t Rp,
-                             int64_t N, int64_t R);
+                             int64_t N, int64_t R, float* MQ);
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st);
 void tc_force_free(TcForce* tf);
 // Test hook: stall_ns > 0 makes later launches issue no copies and end through their
 // timeout path after stall_ns (see fth_test_stall); 0 restores normal launches.
 void tc_force_set_stall(TcForce* tf, uint64_t stall_ns);
+// True when the force adds into MQ (TMA reduce-adds), so the reader must zero MQ after use.
+bool tc_force_accumulates(const TcForce* tf);
 
 struct TcSyrk;
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);

@@ -24,7 +24,7 @@ __device__ __forceinline__ float to_tf32(float x) {
 // operand q^T[r][i] is written as 128-byte runs of i (one replica per warp row).
 template <int NS>
 __global__ void __launch_bounds__(256, 4)
-dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, int mq_planes,
+dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_planes,
                  float* __restrict__ q, float* __restrict__ p, float* __restrict__ s,
                  uint32_t kappa, int flags, int observable, float* __restrict__ ps,
                  int64_t ps_ld, int64_t slot_off, int op_kind, void* op_hi, void* op_lo,
@@ -55,6 +55,8 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, i
             mq4.z += x.z;
             mq4.w += x.w;
         }
+        // the force adds into MQ: leave it zero for the next launch
+        if (flags & kZeroMQ) *reinterpret_cast<float4*>(MQ + off) = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 q4 = *reinterpret_cast<const float4*>(q + off);
         float4 v4[NS];
         v4[0] = *reinterpret_cast<const float4*>(p + off);
@@ -120,7 +122,7 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, const float* __restrict__ MQ, i
 }
 
 cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
-                             const float* MQ, int mq_planes, float* q, float* p, float* s,
+                             float* MQ, int mq_planes, float* q, float* p, float* s,
                              uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,

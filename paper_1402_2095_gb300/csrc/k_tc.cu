@@ -329,6 +329,192 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
     tc_teardown<KIND, BN>(tmem);
 }
 
+// ------------------------------------------------------------------ row-pair force GEMM
+// TF32, Rp in (128, 256], Np a multiple of 256.  A CTA takes two neighbouring 128-row blocks
+// (rows rb0 * 128 .. + 255) over one of KSPLIT K shares: every q^T slice it loads feeds
+// both blocks' MMAs (two 128 x 256 TMEM accumulators, all 512 columns), so a CTA takes in a
+// third fewer operand bytes per flop than with one row block -- the operand intake of the
+// SMs, not DRAM or L2 bandwidth, is what bounds the one-block kernel.  The partial tiles
+// are added into MQ in L2 by TMA tensor reduce-adds from shared memory (SWIZZLE_128B boxes
+// of 128 rows x 32 columns); MQ is zero at every launch (the element-wise step that reads
+// it writes zeros back).  The order of the KSPLIT additions into an element is not fixed,
+// so MQ can differ in its last bits from run to run.
+template <int STAGES, int KSPLIT>
+__global__ void __launch_bounds__(128, 1)
+tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ CUtensorMap mq,
+                     int Rp, int nslices_total, uint32_t* err, uint64_t stall_ns) {
+    constexpr int kA = 128 * 128;               // one 128-row x 128-B slice of M
+    constexpr int kB = 256 * 128;               // 256 replica rows x 128 B of q^T
+    constexpr int kStage = 2 * kA + kB;         // 64 KiB
+    constexpr int kBox = 128 * 128;             // staged box: 128 rows x 32 FP32 columns
+    static_assert(STAGES * kStage >= 8 * kBox, "stage space for one staged tile");
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* stages = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(stages + STAGES * kStage);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = full + 2 * STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2 * STAGES + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    // programmatic dependent launch: the setup above overlaps the previous kernel's tail;
+    // q^T and MQ are touched only after the wait (the producer waits below)
+    if (threadIdx.x != 0) {
+        grid_dependency_wait();
+        allow_dependent_launch();   // the element-wise kernel waits for this grid's end
+    }
+    const int rb0 = blockIdx.x * 2;             // first of the two 128-row blocks
+    const int kc = blockIdx.y;
+    const int s0 = (nslices_total * kc) / KSPLIT;
+    const int nsl = (nslices_total * (kc + 1)) / KSPLIT - s0;
+    const uint64_t loop_ns = stall_ns ? stall_ns : kWaitNs;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        if (stall_ns) {
+            grid_dependency_wait();
+            allow_dependent_launch();
+            if (nsl > 0) mbar_wait(&empty[0], 0, err, loop_ns);
+        } else {
+            const int early = std::min(STAGES, nsl);
+            // M slices of the first ring fill (no earlier kernel writes M) before the wait
+            for (int kb = 0; kb < early; ++kb) {
+                uint8_t* base = stages + kb * kStage;
+                mbar_expect_tx(&full[kb], kStage);
+                tma_load_3d(&maps.a_hi, &full[kb], base, 0, 0, rb0 * nslices_total + s0 + kb);
+                tma_load_3d(&maps.a_hi, &full[kb], base + kA, 0, 0,
+                            (rb0 + 1) * nslices_total + s0 + kb);
+            }
+            grid_dependency_wait();
+            allow_dependent_launch();
+            int issued = 0;
+            bool ok = true;
+            for (int kb = 0; kb < nsl && ok; ++kb) {
+                const int st = kb % STAGES;
+                if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
+                if (!ok) break;
+                uint8_t* base = stages + st * kStage;
+                if (kb >= early) {
+                    mbar_expect_tx(&full[st], kStage);
+                    tma_load_3d(&maps.a_hi, &full[st], base, 0, 0, rb0 * nslices_total + s0 + kb);
+                    tma_load_3d(&maps.a_hi, &full[st], base + kA, 0, 0,
+                                (rb0 + 1) * nslices_total + s0 + kb);
+                }
+                tma_load_2d(&maps.b_hi, &full[st], base + 2 * kA, (s0 + kb) * 32, 0);
+                ++issued;
+            }
+            if (!ok || *reinterpret_cast<volatile uint32_t*>(err) != 0) {
+                // drain the copies still in flight before the CTA exits (bounded)
+                for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
+                    mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: block rb0 into TMEM columns 0..255, block rb0 + 1 into 256..511
+        constexpr uint32_t idesc = make_idesc(2, 256);
+        bool ok = true;
+        for (int kb = 0; kb < nsl; ++kb) {
+            const int st = kb % STAGES;
+            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err, loop_ns)) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t base = smem_u32(stages + st * kStage);
+            const uint64_t a0 = sw128_desc(base);
+            const uint64_t a1 = sw128_desc(base + kA);
+            const uint64_t b = sw128_desc(base + 2 * kA);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA K step
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                umma<1>(tmem, a0 + adv, b + adv, idesc, acc);
+                umma<1>(tmem + 256u, a1 + adv, b + adv, idesc, acc);
+            }
+            umma_commit(&empty[st]);
+        }
+        // always signal: the commit also tracks completion of every MMA issued above
+        umma_commit(done);
+        if (!ok) atomicOr(err, kErrTimeout);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    fence_after_sync();
+    __syncthreads();                            // every stage consumed: reuse them for staging
+    if (ok && nsl > 0) {
+        // four chunks of 128 columns (two per tile), staged alternately in two 64 KiB
+        // buffers: a chunk's reduce-adds run while the next chunk is read out of TMEM
+        const int r = warp * 32 + lane;         // row within the 128-row block (TMEM lane)
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int t = q >> 1, half = q & 1;
+            uint8_t* buf = stages + (q & 1) * 4 * kBox;
+            if (q >= 2) {
+                // the reduce-adds of chunk q - 2 have read this buffer
+                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                __syncthreads();
+            }
+#pragma unroll 1
+            for (int g4 = 0; g4 < 2; ++g4) {
+                uint32_t v[4][16];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) +
+                                        (uint32_t)(t * 256 + half * 128 + g4 * 64 + u * 16),
+                                    v[u]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    // columns 16 (4 g4 + u) .. + 15 of this chunk: box (2 g4 + u / 2), chunks
+                    // (u & 1) * 4 .. + 3 of the row, each at j ^ (row mod 8) (SWIZZLE_128B)
+                    uint8_t* box = buf + (2 * g4 + (u >> 1)) * kBox + r * 128;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int chunk = (u & 1) * 4 + j;
+                        *reinterpret_cast<uint4*>(box + ((chunk ^ (r & 7)) << 4)) =
+                            make_uint4(v[u][4 * j], v[u][4 * j + 1], v[u][4 * j + 2], v[u][4 * j + 3]);
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int b = 0; b < 4; ++b) {
+                    const int col = half * 128 + b * 32;
+                    if (col < Rp) tma_reduce_add_2d(&mq, buf + b * kBox, col, (rb0 + t) * 128);
+                }
+                bulk_commit_group();
+            }
+        }
+        if (threadIdx.x == 0) bulk_wait_all();
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------ SYRK accumulator
 // One CTA per upper tile (I <= J): tiles[t][a][b] += sum_c ps[I*128+a][c] ps[J*128+b][c].
 template <int STAGES>
@@ -624,10 +810,12 @@ size_t tc_smem_bytes() {
 }  // namespace
 
 struct TcForce {
+    CUtensorMap mq;     // MQ as 128-row x 32-column SWIZZLE_128B boxes (row-pair kernel)
     TcMaps maps;        // B box of kForceBN rows (column-tiled kernel)
     TcMaps maps_wide;   // B box of kWideBN rows (split-K kernel, Rp <= kWideBN)
     int kind;
     bool wide;
+    bool pair;          // TF32 row-pair kernel with L2 reduce-adds (MQ zeroed by its reader)
     int64_t Np, Rp, N, R;
     uint64_t stall_ns = 0;   // test hook: > 0 makes the launches end through their timeout path
 };
@@ -640,7 +828,7 @@ struct TcSyrk {
 
 cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const void* A_lo,
                              const void* B_hi, const void* B_lo, int64_t Np, int64_t Rp,
-                             int64_t N, int64_t R) {
+                             int64_t N, int64_t R, float* MQ) {
     TcForce* tf = new TcForce();
     tf->kind = kind;
     tf->Np = Np;
@@ -664,6 +852,9 @@ cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const vo
         if (e == cudaSuccess && bf) e = make_map(&tf->maps_wide.b_lo, B_lo, bf, Np, Rp, Np, kWideBN);
         if (!bf) tf->maps_wide.b_lo = tf->maps_wide.b_hi;
     }
+    // TF32 with whole pairs of row blocks: the row-pair kernel
+    tf->pair = tf->wide && !bf && Np % 256 == 0 && MQ != nullptr;
+    if (e == cudaSuccess && tf->pair) e = make_map(&tf->mq, MQ, 0, Rp, Np, Rp, 128);
 
     if (e != cudaSuccess) {
         delete tf;
@@ -699,8 +890,34 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
 }
 
 
+constexpr int kPairStages = 3;
+constexpr int kPairKSplit = 8;
+
+static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st) {
+    const size_t sm = (size_t)kPairStages * (2 * 128 * 128 + 256 * 128) + 1024 +
+                      8 * (2 * kPairStages + 2);
+    auto kern = tc_force_pair_kernel<kPairStages, kPairKSplit>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(tf->Np / 256), kPairKSplit, 1);
+    cfg.blockDim = dim3(128, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, tf->mq, (int)tf->Rp, (int)(tf->Np / 32),
+                              err, tf->stall_ns);
+}
+
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
                          cudaStream_t st) {
+    if (tf->pair) {
+        const cudaError_t e = launch_pair(tf, err, st);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     if (tf->wide) {
         cudaError_t e = tf->kind == 1 ? launch_splitk<1, 4>(tf, MQ, ldf, err, st)
                                       : launch_splitk<2, 2>(tf, MQ, ldf, err, st);
@@ -729,6 +946,8 @@ cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* er
 void tc_force_free(TcForce* tf) { delete tf; }
 
 void tc_force_set_stall(TcForce* tf, uint64_t stall_ns) { tf->stall_ns = stall_ns; }
+
+bool tc_force_accumulates(const TcForce* tf) { return tf->pair; }
 
 cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld) {
     TcSyrk* ts = new TcSyrk();
