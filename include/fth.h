@@ -66,7 +66,12 @@ enum fth_dtype { FTH_F32 = 0, FTH_F64 = 1 };
  *   FP32    plain FP32 FFMA GEMM / SpMM;
  *   TF32    tcgen05 kind::tf32 tensor-core GEMM (dense only);
  *   BF16X3  tcgen05 kind::f16 with split BF16 operands, hi*hi + hi*lo + lo*hi (dense only);
- *   FP64    FP64 state and arithmetic, one CTA per replica (dense, N <= 1024).     */
+ *   FP64    FP64 state and arithmetic, one CTA per replica (dense, N <= 1024).
+ * With FTH_TRACK_ALL the TF32 and BF16X3 forms also accumulate every element on the
+ * tensor cores: the samples are staged rounded to nearest BF16 (8 significant bits) and
+ * their products summed in FP32.  A product's rounding error is at most 2^-7 of it and
+ * averages out over samples up to a bias of order 1e-5 of the element (Gaussian
+ * samples: about -4.5e-6); FP32 accumulates in FFMA, FP64 in FP64.     */
 enum fth_precision { FTH_PREC_FP32 = 0, FTH_PREC_TF32 = 1, FTH_PREC_BF16X3 = 2, FTH_PREC_FP64 = 3 };
 
 /* Which elements of <x x^T> are accumulated (sized at create, paper's "2A" reals):

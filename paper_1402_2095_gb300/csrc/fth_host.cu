@@ -51,6 +51,12 @@ struct Layout {
     size_t total = 0;
 };
 
+// The tensor-core paths accumulate every element from a BF16 stack of samples.
+bool bf16_stack(const Layout& L) {
+    return L.path == kPathDense32 && L.track == FTH_TRACK_ALL &&
+           (L.precision == FTH_PREC_TF32 || L.precision == FTH_PREC_BF16X3);
+}
+
 struct Carve {
     size_t off = 0;
     size_t take(size_t bytes) {
@@ -290,8 +296,10 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         }
     }
     if (L->path != kPathDense64) {
+        // auto: 2048 FP32 or 4096 BF16 staged columns (8 KiB per row) per pass
+        const int64_t cols = bf16_stack(*L) ? 4096 : 2048;
         L->stack = o->stack > 0 ? o->stack
-                                : (all32 ? std::max<int64_t>(1, 2048 / L->Rp) : 4);
+                                : (all32 ? std::max<int64_t>(1, cols / L->Rp) : 4);
         L->ps_ld = L->stack * L->Rp;
     }
 
@@ -311,8 +319,9 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
             L->off_ophi = c.take((size_t)Rp * Np * esz);
             if (o->precision == FTH_PREC_BF16X3) L->off_oplo = c.take((size_t)Rp * Np * esz);
         }
-        L->off_ps = c.take((size_t)Np * L->ps_ld * 4);
-        L->off_ps1 = c.take((size_t)Np * L->ps_ld * 4);
+        const size_t ps_esz = bf16_stack(*L) ? 2 : 4;
+        L->off_ps = c.take((size_t)Np * L->ps_ld * ps_esz);
+        L->off_ps1 = c.take((size_t)Np * L->ps_ld * ps_esz);
     } else if (L->path == kPathCsr) {
         L->off_rowptr = c.take((size_t)(N + 1) * 4);
         L->off_col = c.take((size_t)std::max<int64_t>(L->nnz, 1) * 4);
@@ -660,10 +669,9 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
         fth_status st = force(c);
         if (st != FTH_OK) return st;
         const bool take = c->nsamp >= c->burnin;
-        // the tcgen05 accumulation pass reads the samples as TF32: round them to nearest
-        const bool tf32_samples = is_tc(c) && L.track == FTH_TRACK_ALL;
+        // the tcgen05 accumulation pass reads a BF16 stack (samples rounded to nearest)
         const int flags = kDoEnd | kDoStart | (take ? kDoSample : 0) |
-                          (take && tf32_samples ? kSampleTf32 : 0) | zero_mq(c);
+                          (take && bf16_stack(L) ? kSampleBf16 : 0) | zero_mq(c);
         if (take && c->nfill == 0) {
             st = claim_stack(c);
             if (st != FTH_OK) return st;
@@ -1097,8 +1105,9 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
                                   c->MQ),
                  "tensor maps (force)");
         if (L.track == FTH_TRACK_ALL) {
-            FTH_CK_C(tc_syrk_prepare(&c->tcs, c->psb[0], L.Np, L.ps_ld), "tensor maps (syrk)");
-            FTH_CK_C(tc_syrk_prepare(&c->tcs1, c->psb[1], L.Np, L.ps_ld), "tensor maps (syrk)");
+            float* tiles = static_cast<float*>(c->partial);
+            FTH_CK_C(tc_syrk_prepare(&c->tcs, c->psb[0], L.Np, L.ps_ld, tiles), "tensor maps (syrk)");
+            FTH_CK_C(tc_syrk_prepare(&c->tcs1, c->psb[1], L.Np, L.ps_ld, tiles), "tensor maps (syrk)");
         }
     }
 #undef FTH_CK_C

@@ -66,12 +66,12 @@ cudaError_t launch_dense_prepare(const void* src, int f64, int64_t n, int64_t r0
                                  int64_t Np, int layout, void* hi, void* lo, uint32_t* flags,
                                  cudaStream_t st);
 
-// Flags of the dense element-wise GLE kernel.  kSampleTf32: stage the samples rounded
-// to TF32 (round to nearest), because the tensor-core accumulation pass reads them as
-// kind::tf32 operands and the MMA drops the low 13 mantissa bits (truncation, a bias of
-// ~7e-4 per product otherwise).  kZeroMQ: write zeros over MQ after reading it (the force
-// adds its partial sums into MQ).
-enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleTf32 = 8, kZeroMQ = 16 };
+// Flags of the dense element-wise GLE kernel.  kSampleBf16: stage the samples in a BF16
+// stack, rounded to nearest, for the tensor-core accumulation pass (kind::f16 operands:
+// twice the TF32 MMA rate and half the bytes; the rounding errors average out over the
+// samples up to a bias of order 1e-5 of each element).
+// kZeroMQ: write zeros over MQ after reading it (the force adds its partial sums into MQ).
+enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleBf16 = 8, kZeroMQ = 16 };
 
 // Operand copies of q the element-wise kernel writes for the force GEMM.
 enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
@@ -167,7 +167,8 @@ void tc_force_set_stall(TcForce* tf, uint64_t stall_ns);
 bool tc_force_accumulates(const TcForce* tf);
 
 struct TcSyrk;
-cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld);
+cudaError_t tc_syrk_prepare(TcSyrk** out, const void* ps, int64_t Np, int64_t ps_ld,
+                            float* tiles);
 cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t* err,
                         cudaStream_t st);
 void tc_syrk_free(TcSyrk* ts);

@@ -89,13 +89,19 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_
         *reinterpret_cast<float4*>(p + off) = v4[0];
 #pragma unroll
         for (int a = 1; a < NS; ++a) *reinterpret_cast<float4*>(s + (a - 1) * plane + off) = v4[a];
-        if (flags & kSampleTf32) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) samp[e] = to_tf32(samp[e]);
-        }
-        if (flags & kDoSample)
+        if ((flags & kDoSample) && (flags & kSampleBf16)) {
+            // BF16 stack of the tensor-core accumulation pass, rounded to nearest
+            const __nv_bfloat162 s01 = __floats2bfloat162_rn(samp[0], samp[1]);
+            const __nv_bfloat162 s23 = __floats2bfloat162_rn(samp[2], samp[3]);
+            uint2 v;
+            v.x = *reinterpret_cast<const uint32_t*>(&s01);
+            v.y = *reinterpret_cast<const uint32_t*>(&s23);
+            *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(ps) + (int64_t)i * ps_ld +
+                                      slot_off + r0) = v;
+        } else if (flags & kDoSample) {
             *reinterpret_cast<float4*>(ps + (int64_t)i * ps_ld + slot_off + r0) =
                 make_float4(samp[0], samp[1], samp[2], samp[3]);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) qn[e] = qa[e];
     }

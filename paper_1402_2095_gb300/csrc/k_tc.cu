@@ -28,15 +28,17 @@ using namespace tc;
 
 // ------------------------------------------------------------------ shared mainloop
 // KIND 1: TF32, one A and one B operand.  KIND 2: split BF16, A = (hi, lo),
-// B = (hi, lo), three products hi*hi + hi*lo + lo*hi per K slice.
+// B = (hi, lo), three products hi*hi + hi*lo + lo*hi per K slice.  KIND 3: one BF16 A
+// and B operand (the accumulation pass over the BF16 sample stack).
 template <int KIND, int BN>
 struct TcCfg {
-    static constexpr int kOps = KIND == 1 ? 1 : 2;               // operand planes
+    static constexpr int kOps = KIND == 2 ? 2 : 1;               // operand planes
     static constexpr int kABytes = 128 * 128;                     // one 128-row x 128-B slice
     static constexpr int kBBytes = BN * 128;
     static constexpr int kStageBytes = kOps * (kABytes + kBBytes);
     static constexpr int kKPerSlice = KIND == 1 ? 32 : 64;       // elements per 128 B
     static constexpr int kKPerMma = KIND == 1 ? 8 : 16;
+    static constexpr int kMmaPerSlice = 4;                        // 32 bytes of K each
     static constexpr int kTmemCols = BN < 32 ? 32 : BN;
 };
 
@@ -128,11 +130,13 @@ __device__ __forceinline__ void tc_mainloop(const TcMaps& maps, int a_row, int b
             const uint64_t ah = sw128_desc(base);
             const uint64_t bh = sw128_desc(base + C::kABytes);
 #pragma unroll
-            for (int kk = 0; kk < 128 / (C::kKPerMma * (KIND == 1 ? 4 : 2)); ++kk) {
+            for (int kk = 0; kk < C::kMmaPerSlice; ++kk) {
                 const uint64_t adv = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA K step
                 const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
                 if (KIND == 1) {
                     umma<1>(tmem, ah + adv, bh + adv, idesc, acc);
+                } else if (KIND == 3) {
+                    umma<2>(tmem, ah + adv, bh + adv, idesc, acc);
                 } else {
                     const uint64_t al = sw128_desc(base + C::kABytes + C::kBBytes);
                     const uint64_t bl = sw128_desc(base + 2 * C::kABytes + C::kBBytes);
@@ -524,14 +528,14 @@ tc_syrk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, i
     uint8_t* stages;
     uint64_t *full, *empty, *done;
     uint32_t tmem;
-    tc_setup<1, 128, STAGES>(stages, full, empty, done, tmem);
+    tc_setup<3, 128, STAGES>(stages, full, empty, done, tmem);
     int t = blockIdx.x, I = 0;
     while (t >= nbt - I) {
         t -= nbt - I;
         ++I;
     }
     const int J = I + t;
-    tc_mainloop<1, 128, STAGES>(maps, I * 128, J * 128, nslices, stages, full, empty, done, tmem,
+    tc_mainloop<3, 128, STAGES>(maps, I * 128, J * 128, nslices, stages, full, empty, done, tmem,
                                 err);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -554,7 +558,7 @@ tc_syrk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, i
             }
         }
     }
-    tc_teardown<1, 128>(tmem);
+    tc_teardown<3, 128>(tmem);
 }
 
 // 128 x 256 tiles: rows I*128.., columns J'*256.. covering packed tiles (I, 2J') and
@@ -567,7 +571,7 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
     uint8_t* stages;
     uint64_t *full, *empty, *done;
     uint32_t tmem;
-    tc_setup<1, 256, STAGES>(stages, full, empty, done, tmem);
+    tc_setup<3, 256, STAGES>(stages, full, empty, done, tmem);
     const int nbw = (nbt + 1) / 2;
     int t = blockIdx.x, I = 0;
     while (t >= nbw - I / 2) {
@@ -575,7 +579,7 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
         ++I;
     }
     const int Jw = I / 2 + t;
-    tc_mainloop<1, 256, STAGES>(maps, I * 128, Jw * 256, nslices, stages, full, empty, done, tmem,
+    tc_mainloop<3, 256, STAGES>(maps, I * 128, Jw * 256, nslices, stages, full, empty, done, tmem,
                                 err);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
@@ -604,28 +608,37 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
             }
         }
     }
-    tc_teardown<1, 256>(tmem);
+    tc_teardown<3, 256>(tmem);
 }
 
 // 256 x 256 output blocks (Iw <= Jw in 256-row units): two 128 x 256 accumulators (all
 // 512 TMEM columns) share each B slice, so a CTA takes 64 KiB of operands per K slice for
-// twice the MMAs of the 128 x 256 form (a third fewer operand bytes per flop) and the
-// upper triangle fits one wave of CTAs.  On the diagonal A and B are the same rows and
-// one load serves both.  Needs an even number of 128-row blocks.
-template <int STAGES>
-__global__ void __launch_bounds__(128, 1)
-tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, int nbt,
-                  int nslices, uint32_t* err) {
+// twice the MMAs of the 128 x 256 form (a third fewer operand bytes per flop).  On the
+// diagonal A and B are the same rows and one load serves both.  Needs an even number of
+// 128-row blocks.  CTA c takes blocks c, c + G, c + 2G ... (G = the number of blocks when
+// they fit one wave).  Warp 4 lane 0 issues the copies (running ahead into the next block
+// while the accumulator drains), warp 5 lane 0 the MMAs, warps 0..3 (one TMEM lane
+// quadrant each) drain the accumulator: 128-row x 32-column boxes staged in shared memory
+// (SWIZZLE_128B, OUTB buffers) are added into the FP32 partial tiles in L2 by TMA tensor
+// reduce-adds, so the read-modify-write of the partial sums never passes through the SM.
+template <int STAGES, int OUTB>
+__global__ void __launch_bounds__(192, 1)
+tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ CUtensorMap part,
+                  int nbt, int nslices, uint32_t* err) {
     constexpr int kSlab = 256 * 128;            // one 256-row x 128-byte K slice
     constexpr int kStage = 2 * kSlab;           // A rows, then B rows
+    constexpr int kBox = 128 * 128;             // staged box: 128 rows x 32 FP32 columns
     constexpr uint32_t kCols = 512;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* stages = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(stages + STAGES * kStage);
+    uint8_t* stage_out = stages + STAGES * kStage;      // [OUTB][kBox]
+    uint64_t* full = reinterpret_cast<uint64_t*>(stage_out + OUTB * kBox);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = full + 2 * STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2 * STAGES + 1);
+    uint64_t* tfull = full + 2 * STAGES;        // MMA -> epilogue
+    uint64_t* tempty = tfull + 1;               // epilogue -> MMA
+    uint64_t* drain = tfull + 2;                // MMA completion after a timed-out wait
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfull + 3);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -638,7 +651,9 @@ tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 128);
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -646,97 +661,139 @@ tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
-
     const int nbw = nbt / 2;
-    int t = blockIdx.x, Iw = 0;
-    while (t >= nbw - Iw) {
-        t -= nbw - Iw;
-        ++Iw;
-    }
-    const int Jw = Iw + t;
-    const bool diag = Iw == Jw;
+    const int nblk = nbw * (nbw + 1) / 2;
+    auto decode = [nbw](int t, int& Iw, int& Jw) {
+        Iw = 0;
+        while (t >= nbw - Iw) {
+            t -= nbw - Iw;
+            ++Iw;
+        }
+        Jw = Iw + t;
+    };
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 4 && lane == 0) {
         // TMA producer
-        int issued = 0;
+        int c = 0;
         bool ok = true;
-        for (int kb = 0; kb < nslices && ok; ++kb) {
-            const int st = kb % STAGES;
-            if (kb >= STAGES) ok = mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, err);
-            if (!ok) break;
-            uint8_t* base = stages + st * kStage;
-            mbar_expect_tx(&full[st], diag ? kSlab : kStage);
-            tma_load_2d(&maps.b_hi, &full[st], base + kSlab, kb * 32, Jw * 256);
-            if (!diag) tma_load_2d(&maps.b_hi, &full[st], base, kb * 32, Iw * 256);
-            ++issued;
+        for (int t = blockIdx.x; t < nblk && ok; t += gridDim.x) {
+            int Iw, Jw;
+            decode(t, Iw, Jw);
+            const bool diag = Iw == Jw;
+            for (int kb = 0; kb < nslices; ++kb, ++c) {
+                const int st = c % STAGES;
+                if (c >= STAGES) ok = mbar_wait(&empty[st], ((c / STAGES) + 1) & 1, err);
+                if (!ok) break;
+                uint8_t* base = stages + st * kStage;
+                mbar_expect_tx(&full[st], diag ? kSlab : kStage);
+                tma_load_2d(&maps.b_hi, &full[st], base + kSlab, kb * 64, Jw * 256);
+                if (!diag) tma_load_2d(&maps.b_hi, &full[st], base, kb * 64, Iw * 256);
+            }
         }
         if (!ok || *reinterpret_cast<volatile uint32_t*>(err) != 0) {
-            for (int kb = std::max(0, issued - STAGES); kb < issued; ++kb)
-                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+            // drain the copies still in flight before the CTA exits (bounded)
+            for (int k = c > STAGES ? c - STAGES : 0; k < c; ++k)
+                mbar_wait(&full[k % STAGES], (k / STAGES) & 1, err);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: rows Iw*256 + 0..127 into columns 0..255, rows + 128..255 into
-        // columns 256..511
-        constexpr uint32_t idesc = make_idesc(2, 256);
+    } else if (warp == 5 && lane == 0) {
+        // MMA issuer (BF16 operands): rows Iw*256 + 0..127 into columns 0..255, rows
+        // + 128..255 into columns 256..511
+        constexpr uint32_t idesc = make_idesc(1, 256);
+        int c = 0, u = 0;
         bool ok = true;
-        for (int kb = 0; kb < nslices; ++kb) {
-            const int st = kb % STAGES;
-            if (!mbar_wait(&full[st], (kb / STAGES) & 1, err)) {
-                ok = false;
-                break;
-            }
+        for (int t = blockIdx.x; t < nblk && ok; t += gridDim.x, ++u) {
+            int Iw, Jw;
+            decode(t, Iw, Jw);
+            const bool diag = Iw == Jw;
+            // the previous block's accumulator has been read out
+            if (u >= 1) ok = mbar_wait(tempty, (u - 1) & 1, err);
+            if (!ok) break;
             fence_after_sync();
-            const uint32_t base = smem_u32(stages + st * kStage);
-            const uint32_t abase = diag ? base + kSlab : base;
-            const uint64_t a0 = sw128_desc(abase);
-            const uint64_t a1 = sw128_desc(abase + 128 * 128);
-            const uint64_t b = sw128_desc(base + kSlab);
+            for (int kb = 0; kb < nslices; ++kb, ++c) {
+                const int st = c % STAGES;
+                if (!mbar_wait(&full[st], (c / STAGES) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t base = smem_u32(stages + st * kStage);
+                const uint32_t abase = diag ? base + kSlab : base;
+                const uint64_t a0 = sw128_desc(abase);
+                const uint64_t a1 = sw128_desc(abase + 128 * 128);
+                const uint64_t b = sw128_desc(base + kSlab);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t adv = (uint64_t)((kk * 32) >> 4);
-                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                umma<1>(tmem, a0 + adv, b + adv, idesc, acc);
-                umma<1>(tmem + 256, a1 + adv, b + adv, idesc, acc);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    umma<2>(tmem, a0 + adv, b + adv, idesc, acc);
+                    umma<2>(tmem + 256, a1 + adv, b + adv, idesc, acc);
+                }
+                umma_commit(&empty[st]);
             }
-            umma_commit(&empty[st]);
+            if (ok) umma_commit(tfull);
         }
-        umma_commit(done);
-        if (!ok) atomicOr(err, kErrTimeout);
-    }
-    __syncwarp();
-
-    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
-    fence_after_sync();
-    if (ok) {
+        if (!ok) {
+            // let every MMA issued so far finish before the tensor memory is freed
+            atomicOr(err, kErrTimeout);
+            umma_commit(drain);
+            mbar_wait(drain, 0, err);
+        }
+    } else if (warp < 4) {
+        // epilogue: warp w reads TMEM lanes 32 w .. + 31 (rows of both 128-row halves)
+        const int r = warp * 32 + lane;
+        int u = 0, nbox = 0;
+        for (int t = blockIdx.x; t < nblk; t += gridDim.x, ++u) {
+            int Iw, Jw;
+            decode(t, Iw, Jw);
+            // uniform over the four warps: the box loop below has named barriers and
+            // .sync.aligned TMEM loads
+            const bool got = mbar_wait(tfull, u & 1, err);
+            const bool ok = named_barrier_and(1, 128, got && *reinterpret_cast<volatile uint32_t*>(err) == 0);
+            fence_after_sync();
+            if (ok) {
 #pragma unroll 1
-        for (int a = 0; a < 2; ++a) {
-            const int I = 2 * Iw + a;
-#pragma unroll 1
-            for (int half = 0; half < 2; ++half) {
-                const int J = 2 * Jw + half;
-                if (J < I || J >= nbt || I >= nbt) continue;
-                const int64_t tile = (int64_t)I * nbt - ((int64_t)I * (I - 1)) / 2 + (J - I);
-                float* out = tiles + tile * 128 * 128 + (int64_t)(warp * 32 + lane) * 128;
-#pragma unroll 1
-                for (int c = 0; c < 8; ++c) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) +
-                                  (uint32_t)(a * 256 + half * 128 + c * 16),
-                              v);
-                    float4* dst = reinterpret_cast<float4*>(out + c * 16);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float4 o = dst[j];
-                        o.x += v[4 * j];
-                        o.y += v[4 * j + 1];
-                        o.z += v[4 * j + 2];
-                        o.w += v[4 * j + 3];
-                        dst[j] = o;
+                for (int q = 0; q < 16; ++q) {
+                    // box q: accumulator columns 32 q .. + 31 = half-tile (a, half), box b
+                    const int a = q >> 3, half = (q >> 2) & 1, b = q & 3;
+                    const int I = 2 * Iw + a, J = 2 * Jw + half;
+                    if (J < I) continue;                          // below the diagonal
+                    uint8_t* buf = stage_out + (nbox % OUTB) * kBox;
+                    if (nbox >= OUTB) {
+                        // the reduce-add issued OUTB boxes ago has read this buffer
+                        if (threadIdx.x == 0) {
+                            if (OUTB == 2) bulk_wait_read_one();
+                            else bulk_wait_read_all();
+                        }
+                        named_barrier(1, 128);
                     }
+                    uint32_t v[2][16];
+                    const uint32_t col = (uint32_t)(q * 32);
+                    tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + col, v[0]);
+                    tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + col + 16, v[1]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<uint4*>(buf + r * 128 + ((j ^ (r & 7)) << 4)) =
+                            make_uint4(v[j >> 2][4 * (j & 3)], v[j >> 2][4 * (j & 3) + 1],
+                                       v[j >> 2][4 * (j & 3) + 2], v[j >> 2][4 * (j & 3) + 3]);
+                    fence_proxy_async_smem();
+                    named_barrier(1, 128);
+                    if (threadIdx.x == 0) {
+                        const int tile = I * nbt - (I * (I - 1)) / 2 + (J - I);
+                        tma_reduce_add_3d(&part, buf, b * 32, 0, tile);
+                        bulk_commit_group();
+                    }
+                    ++nbox;
                 }
             }
+            fence_before_sync();
+            mbar_arrive(tempty);
+            if (!ok) break;
         }
+        // every reduce-add has landed before the block exits
+        if (threadIdx.x == 0) bulk_wait_all();
     }
+    __syncwarp();
     fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -799,6 +856,7 @@ constexpr int kForceStages = 6;
 constexpr int kSyrkStages = 6;
 constexpr int kSyrkWideStages = 4;
 constexpr int kSyrkSqStages = 3;
+constexpr int kSyrkOutBufs = 2;
 constexpr int kWideBN = 256;
 constexpr int kKSplit = 4;
 
@@ -823,6 +881,7 @@ struct TcForce {
 struct TcSyrk {
     TcMaps maps;        // A and B boxes of 128 rows
     TcMaps maps_wide;   // B box of 256 rows (Np >= 256)
+    CUtensorMap part;   // FP32 partial tiles [ntiles][128][128], boxes of 128 x 32
     int64_t Np, ps_ld;
 };
 
@@ -949,21 +1008,37 @@ void tc_force_set_stall(TcForce* tf, uint64_t stall_ns) { tf->stall_ns = stall_n
 
 bool tc_force_accumulates(const TcForce* tf) { return tf->pair; }
 
-cudaError_t tc_syrk_prepare(TcSyrk** out, const float* ps, int64_t Np, int64_t ps_ld) {
+cudaError_t tc_syrk_prepare(TcSyrk** out, const void* ps, int64_t Np, int64_t ps_ld,
+                            float* tiles) {
     TcSyrk* ts = new TcSyrk();
     ts->Np = Np;
     ts->ps_ld = ps_ld;
-    cudaError_t e = make_map(&ts->maps.a_hi, ps, 0, ps_ld, Np, ps_ld, 128);
+    cudaError_t e = make_map(&ts->maps.a_hi, ps, 1, ps_ld, Np, ps_ld, 128);
     if (e != cudaSuccess) {
         delete ts;
         return e;
+    }
+    {
+        const uint64_t nbt = (uint64_t)(Np / 128);
+        const cuuint64_t dims[3] = {128, 128, nbt * (nbt + 1) / 2};
+        const cuuint64_t strides[2] = {128 * 4, 128 * 128 * 4};
+        const cuuint32_t box[3] = {32, 128, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        auto fn = encode_fn();
+        if (!fn || fn(&ts->part, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, tiles, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            delete ts;
+            return fn ? cudaErrorInvalidValue : cudaErrorNotSupported;
+        }
     }
     ts->maps.b_hi = ts->maps.a_hi;
     ts->maps.a_lo = ts->maps.a_hi;
     ts->maps.b_lo = ts->maps.a_hi;
     ts->maps_wide = ts->maps;
     if (Np >= 256) {
-        e = make_map(&ts->maps_wide.b_hi, ps, 0, ps_ld, Np, ps_ld, 256);
+        e = make_map(&ts->maps_wide.b_hi, ps, 1, ps_ld, Np, ps_ld, 256);
         if (e != cudaSuccess) {
             delete ts;
             return e;
@@ -977,28 +1052,37 @@ cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t*
                         cudaStream_t st) {
     if (ncols <= 0) return cudaSuccess;
     const int nbt = (int)(ts->Np / 128);
-    const int nslices = (int)((ncols + 31) / 32);
+    const int nslices = (int)((ncols + 63) / 64);   // BF16: 64 columns per 128-byte slice
     if (nbt >= 2 && nbt % 2 == 0) {
         const int nbw = nbt / 2;
-        const unsigned nctas = (unsigned)(nbw * (nbw + 1) / 2);
-        const size_t sm = (size_t)kSyrkSqStages * 2 * 256 * 128 + 1024 + 8 * (2 * kSyrkSqStages + 2);
-        auto kern = tc_syrk_sq_kernel<kSyrkSqStages>;
+        const int nblk = nbw * (nbw + 1) / 2;
+        // one CTA per SM at most (shared memory): more blocks than SMs loop
+        static const int nsm = [] {
+            int dev = 0, n = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+            return n > 0 ? n : 1;
+        }();
+        const unsigned grid = (unsigned)std::min(nblk, nsm);
+        const size_t sm = (size_t)kSyrkSqStages * 2 * 256 * 128 + kSyrkOutBufs * 128 * 128 +
+                          1024 + 8 * (2 * kSyrkSqStages + 4);
+        auto kern = tc_syrk_sq_kernel<kSyrkSqStages, kSyrkOutBufs>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<nctas, 128, sm, st>>>(ts->maps_wide, tiles, nbt, nslices, err);
+        kern<<<grid, 192, sm, st>>>(ts->maps_wide, ts->part, nbt, nslices, err);
         return cudaGetLastError();
     }
     if (ts->Np >= 256) {
         const int nbw = (nbt + 1) / 2;
         unsigned nctas = 0;
         for (int I = 0; I < nbt; ++I) nctas += (unsigned)(nbw - I / 2);
-        const size_t sm = tc_smem_bytes<1, 256, kSyrkWideStages>();
+        const size_t sm = tc_smem_bytes<3, 256, kSyrkWideStages>();
         auto kern = tc_syrk_wide_kernel<kSyrkWideStages>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<nctas, 128, sm, st>>>(ts->maps_wide, tiles, nbt, nslices, err);
         return cudaGetLastError();
     }
     const unsigned ntiles = (unsigned)(nbt * (nbt + 1) / 2);
-    const size_t sm = tc_smem_bytes<1, 128, kSyrkStages>();
+    const size_t sm = tc_smem_bytes<3, 128, kSyrkStages>();
     auto kern = tc_syrk_kernel<kSyrkStages>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<ntiles, 128, sm, st>>>(ts->maps, tiles, nbt, nslices, err);

@@ -78,3 +78,11 @@ def trace_terms(n=None, O=None):
     w = np.where(i == j, v, 2.0 * v)
     keep = w != 0
     return np.stack([i[keep], j[keep]], axis=1).astype(np.int64), w[keep]
+
+
+def bf16_rn(x):
+    """x rounded to FP32, then to BF16 with round to nearest, ties to even (returned in
+    float64): the staging of the samples that the tensor-core accumulation pass reads."""
+    u = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)

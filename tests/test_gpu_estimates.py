@@ -1,8 +1,10 @@
 """Estimate-level parity of the force precision forms, full-size checks at the benchmark's
 launch configuration, and the device error paths -- all through the C ABI.
 
-Precision forms (FP32 FFMA, TF32 and split BF16 on tcgen05) change only the force
-contraction (Eq. 5); the estimator is Eq. 6 either way.  Run on the same seed, the
+Precision forms (FP32 FFMA, TF32 and split BF16 on tcgen05) change the force
+contraction (Eq. 5) and, with every element tracked, the tensor-core forms stage the
+samples in BF16 for the accumulation (each product off by at most 2^-7, averaging out
+to ~1e-5 over a run); the estimator is Eq. 6 either way.  Run on the same seed, the
 three forms and the FP64 oracle draw the same Philox normals, so the difference of two
 estimates is (almost) free of statistical error: it isolates what each form's rounding
 does to the estimate of <p_i p_j>.  The bounds are the measured errors with headroom
@@ -19,7 +21,7 @@ import fth_synth as syn
 from oracle import gle, matfun
 from oracle.fth import OracleFTH, fused_step_elements
 
-from gpu_util import gpu_ready
+from gpu_util import bf16_rn, gpu_ready
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not gpu_ready(), reason="needs a CUDA GPU and libfth.so")]
@@ -180,8 +182,9 @@ def test_full_size_dense_tf32_accumulators_sampled():
     """N = 4096, R = 256, TF32 force and every element accumulated (tcgen05 SYRK over
     stacks of 8 samples): three stacked passes and three blocks, read back on a sample
     of 4096 elements.  With A_p = C_p = 0 the dynamics is noise-free velocity Verlet and
-    the samples of q follow in FP64 from the same start; bound 2^-9 of the products'
-    scale (TF32 operands, FP32 sums), on values and block error bars."""
+    the samples of q follow in FP64 from the same start, staged in BF16 (round to nearest)
+    as the accumulation pass reads them; bound 2^-9 of the products' scale (TF32 force,
+    FP32 sums), on values and block error bars."""
     import torch
     from paper_1402_2095_gb300 import FTH
     n, R, K, block = 4096, 256, 24, 8
@@ -210,7 +213,8 @@ def test_full_size_dense_tf32_accumulators_sampled():
     for k in range(K):
         F = q @ M64.T
         p -= 0.5 * dt * F
-        bsum[k // block] += np.einsum("rk,rk->k", q[:, ii], q[:, jj])
+        x = bf16_rn(q)
+        bsum[k // block] += np.einsum("rk,rk->k", x[:, ii], x[:, jj])
         asum += np.einsum("rk,rk->k", np.abs(q[:, ii]), np.abs(q[:, jj]))
         p -= 0.5 * dt * F
         q += dt * p

@@ -17,7 +17,7 @@ import fth_synth as syn
 from oracle import matfun
 from oracle.fth import fused_step_elements
 
-from gpu_util import gpu_ready, make_pair, state_rel_err, trace_terms
+from gpu_util import bf16_rn, gpu_ready, make_pair, state_rel_err, trace_terms
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not gpu_ready(), reason="needs a CUDA GPU and libfth.so")]
@@ -148,12 +148,18 @@ def test_all_elements_one_sample(precision, n):
     f.set_state("q", q0)
     f.run(1)
     q1 = q0 - 0.5 * dt * dt * q0 @ M.T
+    # the tensor-core forms stage the sample in BF16 (round to nearest) for the SYRK
+    x1 = bf16_rn(q1) if precision != "fp32" else q1
     pairs = syn.upper_pairs(n)
     vals, _ = f.elements(pairs)
-    ref = np.einsum("ri,rj->ij", q1, q1)[pairs[:, 0], pairs[:, 1]] / R
+    ref = np.einsum("ri,rj->ij", x1, x1)[pairs[:, 0], pairs[:, 1]] / R
     scale = np.einsum("ri,rj->ij", np.abs(q1), np.abs(q1))[pairs[:, 0], pairs[:, 1]] / R
     bound = 2.0 ** -9 if precision != "fp32" else 1e-6
     assert np.max(np.abs(vals - ref) / scale) <= bound
+    if precision != "fp32":
+        # and not the unrounded products: BF16 staging moves them by up to 2^-7
+        unrounded = np.einsum("ri,rj->ij", q1, q1)[pairs[:, 0], pairs[:, 1]] / R
+        assert np.max(np.abs(vals - unrounded) / scale) > 2.0 ** -12
 
 
 # ------------------------------------------------------------------ stationary estimate
