@@ -37,7 +37,6 @@ struct TcCfg {
     static constexpr int kBBytes = BN * 128;
     static constexpr int kStageBytes = kOps * (kABytes + kBBytes);
     static constexpr int kKPerSlice = KIND == 1 ? 32 : 64;       // elements per 128 B
-    static constexpr int kKPerMma = KIND == 1 ? 8 : 16;
     static constexpr int kMmaPerSlice = 4;                        // 32 bytes of K each
     static constexpr int kTmemCols = BN < 32 ? 32 : BN;
 };
@@ -218,7 +217,9 @@ tc_force_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ MQ, int
                                   0, nslices, false, stall_ns);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    // warp-uniform: tcgen05.ld is .sync.aligned
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, err) &&
+                                                *reinterpret_cast<volatile uint32_t*>(err) == 0);
     fence_after_sync();
     if (ok) {
         const int row = row0 + warp * 32 + lane;
@@ -461,9 +462,10 @@ tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant_
     }
     __syncwarp();
 
-    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
-    fence_after_sync();
-    __syncthreads();                            // every stage consumed: reuse them for staging
+    // block-uniform: the staging loop below has block barriers
+    const bool ok = __syncthreads_and(mbar_wait(done, 0, err) &&
+                                      *reinterpret_cast<volatile uint32_t*>(err) == 0);
+    fence_after_sync();                         // every stage consumed: reuse them for staging
     if (ok && nsl > 0) {
         // four chunks of 128 columns (two per tile), staged alternately in two 64 KiB
         // buffers: a chunk's reduce-adds run while the next chunk is read out of TMEM
@@ -538,7 +540,9 @@ tc_syrk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ tiles, i
     tc_mainloop<3, 128, STAGES>(maps, I * 128, J * 128, nslices, stages, full, empty, done, tmem,
                                 err);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    // warp-uniform: tcgen05.ld is .sync.aligned
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, err) &&
+                                                *reinterpret_cast<volatile uint32_t*>(err) == 0);
     fence_after_sync();
     if (ok) {
         float* out = tiles + (int64_t)blockIdx.x * 128 * 128 + (int64_t)(warp * 32 + lane) * 128;
@@ -582,7 +586,9 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
     tc_mainloop<3, 256, STAGES>(maps, I * 128, Jw * 256, nslices, stages, full, empty, done, tmem,
                                 err);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool ok = mbar_wait(done, 0, err) && *reinterpret_cast<volatile uint32_t*>(err) == 0;
+    // warp-uniform: tcgen05.ld is .sync.aligned
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, err) &&
+                                                *reinterpret_cast<volatile uint32_t*>(err) == 0);
     fence_after_sync();
     if (ok) {
 #pragma unroll 1
