@@ -191,8 +191,11 @@ class Workload:
         if cls in ("syrk_tc", "syrk_fp32"):
             return ("tensor" if cls == "syrk_tc" else "alu", float(n) * (n + 1) * info["stack_cols"])
         if cls == "gle_dense":
-            op = 4 if self.precision in ("tf32", "bf16x3") else 0
-            return ("hbm", float(28 + 24 + 4 + op) * n * R)
+            tc = self.precision in ("tf32", "bf16x3")
+            op = 4 if tc else 0                                  # q^T operand of the force
+            sample = 2 if tc and self.track == "all" else 4      # BF16 or FP32 stack
+            zero = 4 if self.precision == "tf32" else 0          # zeros over MQ (reduce-add force)
+            return ("hbm", float(28 + 24 + sample + op + zero) * n * R)
         if cls == "csr_step":
             return ("hbm", float(24 + 24 + 4) * n * R + 8.0 * self.nnz + 4.0 * n)
         if cls == "pair_accum":
@@ -296,7 +299,8 @@ def roofline(prof, wl, info, peaks, peak_kind):
     burst = peaks["bf16_tflops"]
     fp32_alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if bound == "tensor":
-        tf = wl.precision == "tf32" or name == "syrk_tc"
+        # the accumulation pass multiplies BF16 samples; the force runs in the line's form
+        tf = wl.precision == "tf32" and name != "syrk_tc"
         peak = burst * (tf32_ratio if tf else 1.0)
         out = {"bound": "tensor", "unit": "TFLOP/s", "achieved": amount / per_launch_s / 1e12,
                "peak": peak, "peak_source": f"{peak_kind} bf16 burst"

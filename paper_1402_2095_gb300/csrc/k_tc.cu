@@ -958,13 +958,17 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
 constexpr int kPairStages = 3;
 constexpr int kPairKSplit = 8;
 
-static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st) {
+template <int KS>
+static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t st) {
     const size_t sm = (size_t)kPairStages * (2 * 128 * 128 + 256 * 128) + 1024 +
                       8 * (2 * kPairStages + 2);
-    auto kern = tc_force_pair_kernel<kPairStages, kPairKSplit>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = tc_force_pair_kernel<kPairStages, KS>;
+    static const bool attr_set =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+        cudaSuccess;
+    (void)attr_set;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(tf->Np / 256), kPairKSplit, 1);
+    cfg.gridDim = dim3((unsigned)(tf->Np / 256), KS, 1);
     cfg.blockDim = dim3(128, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
@@ -975,6 +979,14 @@ static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, tf->mq, (int)tf->Rp, (int)(tf->Np / 32),
                               err, tf->stall_ns);
+}
+
+// K split 8 fills the SMs from N = 4096 up (16 row pairs x 8 = 128 CTAs); smaller problems
+// split K 16 ways so they still start about as many CTAs (each CTA's partial tile, and so
+// its epilogue, is the same size either way).
+static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st) {
+    return tf->Np / 256 * kPairKSplit >= 96 ? launch_pair_ks<kPairKSplit>(tf, err, st)
+                                            : launch_pair_ks<2 * kPairKSplit>(tf, err, st);
 }
 
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
