@@ -162,6 +162,31 @@ def test_all_elements_one_sample(precision, n):
         assert np.max(np.abs(vals - unrounded) / scale) > 2.0 ** -12
 
 
+def test_all_elements_one_sample_more_blocks_than_sms():
+    # n = 4608: 171 blocks of 256 x 256 on or above the diagonal, more than the 152 SMs,
+    # so accumulation CTAs loop over several blocks (copies of the next block run ahead
+    # while the accumulator drains).  Same closed form as above, on sampled elements.
+    from paper_1402_2095_gb300 import FTH
+    n, R, dt = 4608, 64, 0.01
+    M = _dense(n, seed=41).astype(np.float32).astype(np.float64)
+    q0 = syn.gaussian_state((R, n), seed=42)
+    z = np.zeros((5, 5))
+    f = FTH(M=M, a_p=z, c_p=z, dt=dt, replicas=R, seed=0, precision="tf32", track="all",
+            block=1, observable="q")
+    f.set_state("q", q0)
+    f.run(1)
+    q1 = q0 - 0.5 * dt * dt * q0 @ M.T
+    x1 = bf16_rn(q1)
+    g = np.random.default_rng(43)
+    pairs = np.concatenate([syn.diag_pairs(n)[g.choice(n, 1024, replace=False)],
+                            syn.random_pairs(n, 60000, seed=44)])
+    vals, _ = f.elements(pairs)
+    i, j = pairs[:, 0], pairs[:, 1]
+    ref = np.einsum("rk,rk->k", x1[:, i], x1[:, j]) / R
+    scale = np.einsum("rk,rk->k", np.abs(q1[:, i]), np.abs(q1[:, j])) / R
+    assert np.max(np.abs(vals - ref) / scale) <= 2.0 ** -9
+
+
 # ------------------------------------------------------------------ stationary estimate
 def _zscores(vals, errs, ref):
     return (vals - ref) / errs
