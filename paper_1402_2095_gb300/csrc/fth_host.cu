@@ -773,7 +773,7 @@ fth_status run_dense64(fth_ctx* c, int64_t steps) {
         {
         ProfScope ps(c, FTH_K_FP64_NOISE);
         FTH_CK(launch_fp64_noise(L.ns, c->g64, L.N, L.Np, L.R, kappa0, seg + (c->primed ? 0 : 1),
-                                 xi, c->stream),
+                                 c->primed ? 0 : 1, xi, c->stream),
                "fp64 noise");
         }
         ++c->launches;

@@ -140,11 +140,13 @@ cudaError_t launch_functional_block(const float* partial32, const double* partia
 cudaError_t launch_round_tf32(float* x, int64_t n, cudaStream_t st);
 cudaError_t launch_split_bf16(const float* x, int64_t n, void* hi, void* lo, cudaStream_t st);
 
-// FP64 small dense path: the normals of a segment are generated ahead over the whole
-// GPU (`xi`: [iters][R][2 ns][Np]), then one CTA per replica runs `nsteps` fused
-// launches (plus the prologue when not primed) reading them.
+// FP64 small dense path: the noise terms of a segment are generated ahead over the whole
+// GPU (`xi`: [iters][R][ns + 1][Np], the normals already multiplied by the O half-steps'
+// noise factors; `prologue`: the first kick is the prologue's single half-step), then one
+// CTA per replica runs `nsteps` fused launches (plus the prologue when not primed).
 cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
-                              uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st);
+                              uint32_t kappa0, int64_t iters, int prologue, double* xi,
+                              cudaStream_t st);
 cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
                               const double* M, double* q, double* p, double* s,
                               const double* noise, int64_t nsteps, int primed_in, int observable,

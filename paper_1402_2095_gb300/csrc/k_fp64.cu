@@ -27,47 +27,93 @@ __device__ __forceinline__ void box_muller64(uint32_t a, uint32_t b, double& z0,
     z1 = rho * sn;
 }
 
-// Noise ahead of the integrator: the NS + 1 normals of every (kappa, i, r) of a segment
-// of `iters` kick indices from kappa0, written to xi[((it R + r) (NS + 1) + a) Np + i]
-// (a fused launch draws its two O half-steps jointly from NS + 1 normals; the prologue
-// uses the first NS).  Replicas share streams in pairs (gle_device.cuh): global replica
-// g = r + roff takes positions (g mod 2) W .. of the stream of pair g / 2, W = NS + 1.
-// FP64 transcendental functions are the bulk of the FP64 path's work; this kernel spreads
-// them over the whole GPU while the integrator (one CTA per replica) stays small.
-// One thread per (it, pair, Philox call k, i), i fastest, so the stores coalesce; each
-// call's four normals go to whichever of the pair's replicas are in this run.
+// Noise ahead of the integrator, already mixed by the O half-steps' noise factors: for
+// every (kappa, i, r) of a segment of `iters` kick indices from kappa0 the kernel draws the
+// W = NS + 1 normals zeta of the replica (replicas share streams in pairs, gle_device.cuh:
+// global replica g = r + roff takes positions (g mod 2) W .. of the stream of pair g / 2)
+// and writes c = L zeta, the noise terms of the two O half-steps drawn jointly (c_0 that of
+// the sample, c_1..NS that of the next state), to xi[((it R + r) W + a) Np + i]; for the
+// prologue's kick (pro0, it = 0) it writes c_1..NS = S zeta_0..NS-1 (one half-step), c_0 = 0.
+// FP64 transcendental functions and these products are the bulk of the FP64 path's work;
+// this kernel spreads them over the whole GPU while the integrator (one CTA per replica)
+// keeps only the state-dependent arithmetic.  One thread per (it, pair, i), i fastest, so
+// the stores coalesce.
 template <int NS>
 __global__ void __launch_bounds__(256)
-fp64_noise_kernel(uint32_t key0, uint32_t key1, uint32_t roff, int N, int Np, int R,
-                  uint32_t kappa0, int iters, double* __restrict__ xi) {
+fp64_noise_kernel(GleF64 g, int N, int Np, int R, uint32_t kappa0, int iters, int pro0,
+                  double* __restrict__ xi) {
     constexpr int W = NS + 1;
     constexpr int kCalls = (2 * W + 3) / 4;
-    const uint32_t j0 = roff >> 1;                           // first pair of this run
-    const int npairs = (int)(((roff + (uint32_t)R - 1u) >> 1) - j0 + 1u);
-    const int64_t total = (int64_t)iters * npairs * kCalls * N;
+    const uint32_t j0 = g.roff >> 1;                         // first pair of this run
+    const int npairs = (int)(((g.roff + (uint32_t)R - 1u) >> 1) - j0 + 1u);
+    const int64_t total = (int64_t)iters * npairs * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % N);
-        int64_t rest = e / N;
-        const int k = (int)(rest % kCalls);
-        rest /= kCalls;
+        const int64_t rest = e / N;
         const uint32_t j = j0 + (uint32_t)(rest % npairs);
         const int it = (int)(rest / npairs);
-        const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i, j,
-                                                 (uint32_t)k), key0, key1);
-        double z[4];
-        box_muller64(x.x, x.y, z[0], z[1]);
-        if (4 * k + 2 < 2 * W) box_muller64(x.z, x.w, z[2], z[3]);
+        double z[4 * kCalls];                                // stream positions 0 .. 2W-1
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int pos = 4 * k + t;
-            if (pos >= 2 * W) continue;
-            const int h = pos >= W ? 1 : 0;
-            const int64_t r = (int64_t)(2u * j + (uint32_t)h) - (int64_t)roff;   // local replica
+        for (int k = 0; k < kCalls; ++k) {
+            const uint4 x = philox4x32_10(make_uint4(kappa0 + (uint32_t)it, (uint32_t)i, j,
+                                                     (uint32_t)k), g.key0, g.key1);
+            box_muller64(x.x, x.y, z[4 * k], z[4 * k + 1]);
+            if (4 * k + 2 < 2 * W) box_muller64(x.z, x.w, z[4 * k + 2], z[4 * k + 3]);
+        }
+        const bool pro = pro0 && it == 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = (int64_t)(2u * j + (uint32_t)h) - (int64_t)g.roff;   // local replica
             if (r < 0 || r >= R) continue;
-            xi[(((int64_t)it * R + r) * W + (pos - h * W)) * Np + i] = z[t];
+            const double* zz = z + h * W;
+            double* out = xi + ((int64_t)it * R + r) * W * Np + i;
+            if (pro) {
+                out[0] = 0.0;
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    double c = 0.0;
+#pragma unroll
+                    for (int b = 0; b <= a; ++b) c = fma(g.S[a * kMaxNs + b], zz[b], c);
+                    out[(int64_t)(a + 1) * Np] = c;
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    double c = 0.0;
+#pragma unroll
+                    for (int b = 0; b <= a; ++b) c = fma(g.L[a * kMaxNs1 + b], zz[b], c);
+                    out[(int64_t)a * Np] = c;
+                }
+            }
         }
     }
+}
+
+// O updates of the FP64 integrator with the noise terms c premixed by fp64_noise_kernel:
+// v <- v + D v + c_1..NS (D = T - I for the prologue's half-step, T T - I for the joint
+// pair), and the sample p = v_0 + (T v)_0 - v_0 + c_0 before it.
+template <int NS>
+__device__ __forceinline__ void o_apply64(double (&v)[NS], const double* D, const double* c) {
+    double out[NS];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        double acc = c[a + 1];
+#pragma unroll
+        for (int b = 0; b < NS; ++b) acc = fma(D[a * kMaxNs + b], v[b], acc);
+        out[a] = v[a] + acc;
+    }
+#pragma unroll
+    for (int a = 0; a < NS; ++a) v[a] = out[a];
+}
+
+template <int NS>
+__device__ __forceinline__ double o_sample64(const double (&v)[NS], const GleF64& g,
+                                             const double* c) {
+    double inc = c[0];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) inc = fma(g.T[b], v[b], inc);
+    return v[0] + inc;
 }
 
 // Shared memory: q and the sample x ([Np] each); when they fit, M transposed
@@ -162,11 +208,11 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
             if (!pro) {
                 // end of the step, sample, start of the next: the two O half-steps jointly
                 v[0] = fma(-g.hdt, mq, v[0]);
-                double pmid;
-                o_joint<NS, double>(v, g, xi, pmid);
+                const double pmid = o_sample64<NS>(v, g, xi);
+                o_apply64<NS>(v, g.D2, xi);
                 xs[i] = observable ? qi : pmid;
             } else {
-                o_half<NS, double>(v, g.T, g.S, xi);
+                o_apply64<NS>(v, g.T, xi);
             }
             v[0] = fma(-g.hdt, mq, v[0]);
             qi = fma(g.dt, v[0], qi);
@@ -195,12 +241,13 @@ fp64_dense_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 
 // Small problems (N <= 32): the FP64 units of an SM sit in its four sub-partitions and a
 // warp issues to one of them, so one warp per replica uses a quarter of the SM's FP64
-// rate.  Here four warps share each replica's work: warp w forms the force over columns
-// k = 8w .. 8w+7 and a quarter of the O-step outputs (pmid and out[0..NS) are NS + 1
-// rows of the joint update, output o to warp o % 4); lane = dof.  State in shared
-// memory, double-buffered between steps; two barriers per step.
-template <int NS>
-__global__ void __launch_bounds__(128)
+// rate.  Here WARPS warps share each replica's work: warp w forms the force over columns
+// k = Cw .. Cw + C - 1 (C = 32 / WARPS) and the O-step outputs o = w, w + WARPS, ... (pmid
+// and out[0..NS) are NS + 1 rows of the joint update, their noise terms premixed by
+// fp64_noise_kernel); lane = dof.  State in shared memory, double-buffered between steps;
+// two barriers per step.
+template <int NS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double* __restrict__ q,
                   double* __restrict__ p, double* __restrict__ s, const double* __restrict__ noise,
                   int iters, int prologue, int observable, const int32_t* __restrict__ pairs,
@@ -208,8 +255,8 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
     extern __shared__ double sh[];
     double* qs = sh;                              // [32]
     double* xs = qs + 32;                         // [32]
-    double* fpart = xs + 32;                      // [4][32]
-    double* vs = fpart + 4 * 32;                  // [2][NS][32]
+    double* fpart = xs + 32;                      // [WARPS][32]
+    double* vs = fpart + WARPS * 32;              // [2][NS][32]
     double* mt = vs + 2 * NS * 32;                // [32][32] (M transposed)
     double* pacc = mt + 32 * 32;                  // [npairs]
     int32_t* pidx = reinterpret_cast<int32_t*>(pacc + npairs);
@@ -224,11 +271,12 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 #pragma unroll
         for (int a = 1; a < NS; ++a) vs[a * 32 + i] = i < N ? s[(a - 1) * plane + base + i] : 0.0;
     }
-    for (int e = tid; e < 32 * 32; e += 128) {
+    constexpr int kThreads = WARPS * 32;
+    for (int e = tid; e < 32 * 32; e += kThreads) {
         const int row = e / 32, k = e % 32;
         mt[k * 32 + row] = (row < N && k < N) ? M[(int64_t)row * Np + k] : 0.0;
     }
-    for (int e = tid; e < npairs; e += 128) {
+    for (int e = tid; e < npairs; e += kThreads) {
         pacc[e] = gacc[e];
         pidx[2 * e] = pairs[2 * e];
         pidx[2 * e + 1] = pairs[2 * e + 1];
@@ -251,18 +299,25 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 #pragma unroll
             for (int a = 0; a < NS + 1; ++a) zn[a] = nz[(int64_t)a * Np];
         }
-        // force, a quarter of the columns per warp
+        // force, 32 / WARPS columns per warp in two FMA chains
         {
+            constexpr int C = 32 / WARPS;
             double f0 = 0.0, f1 = 0.0;
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                f0 = fma(mt[(warp * 8 + k) * 32 + i], qs[warp * 8 + k], f0);
-                f1 = fma(mt[(warp * 8 + k + 1) * 32 + i], qs[warp * 8 + k + 1], f1);
+            for (int k = 0; k < C; k += 2) {
+                f0 = fma(mt[(warp * C + k) * 32 + i], qs[warp * C + k], f0);
+                f1 = fma(mt[(warp * C + k + 1) * 32 + i], qs[warp * C + k + 1], f1);
             }
             fpart[warp * 32 + i] = f0 + f1;
         }
         __syncthreads();
-        const double mq = (fpart[i] + fpart[32 + i]) + (fpart[64 + i] + fpart[96 + i]);
+        double mq;
+        if (WARPS == 4) {
+            mq = (fpart[i] + fpart[32 + i]) + (fpart[64 + i] + fpart[96 + i]);
+        } else {
+            mq = ((fpart[i] + fpart[32 + i]) + (fpart[64 + i] + fpart[96 + i])) +
+                 ((fpart[128 + i] + fpart[160 + i]) + (fpart[192 + i] + fpart[224 + i]));
+        }
         const double* vc = vs + cb * NS * 32;
         double* vn = vs + (cb ^ 1) * NS * 32;
         double v[NS];
@@ -271,10 +326,10 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         if (!pro) v[0] = fma(-g.hdt, mq, v[0]);   // B(dt/2), end of the step (not in the prologue)
 #pragma unroll
         for (int o = 0; o <= NS; ++o) {
-            if ((o & 3) != warp) continue;
+            if (o % WARPS != warp) continue;
             if (o == 0) {
                 if (!pro) {
-                    double u = g.L[0] * z[0];
+                    double u = z[0];                       // premixed noise of the sample
 #pragma unroll
                     for (int b = 0; b < NS; ++b) u = fma(g.T[b], v[b], u);
                     if (!observable) xs[i] = v[0] + u;
@@ -282,18 +337,10 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
                 continue;
             }
             const int a = o - 1;
-            double acc = 0.0;
-            if (pro) {
+            double acc = z[a + 1];                         // premixed noise term
+            const double* D = pro ? g.T : g.D2;
 #pragma unroll
-                for (int b = 0; b < NS; ++b) acc = fma(g.T[a * kMaxNs + b], v[b], acc);
-#pragma unroll
-                for (int b = 0; b <= a; ++b) acc = fma(g.S[a * kMaxNs + b], z[b], acc);
-            } else {
-#pragma unroll
-                for (int b = 0; b < NS; ++b) acc = fma(g.D2[a * kMaxNs + b], v[b], acc);
-#pragma unroll
-                for (int b = 0; b <= a + 1; ++b) acc = fma(g.L[(a + 1) * kMaxNs1 + b], z[b], acc);
-            }
+            for (int b = 0; b < NS; ++b) acc = fma(D[a * kMaxNs + b], v[b], acc);
             double va = v[a] + acc;
             if (a == 0) {
                 // B(dt/2) and A(dt) of the next step; the sample of q is the position before A
@@ -307,12 +354,12 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
         __syncthreads();
         const int f = prologue ? it - 1 : it;
         if (!pro && f >= acc_from)
-            for (int e = tid; e < npairs; e += 128)
+            for (int e = tid; e < npairs; e += kThreads)
                 pacc[e] = fma(xs[pidx[2 * e]], xs[pidx[2 * e + 1]], pacc[e]);
         cb ^= 1;
     }
     __syncthreads();
-    for (int e = tid; e < npairs; e += 128) gacc[e] = pacc[e];
+    for (int e = tid; e < npairs; e += kThreads) gacc[e] = pacc[e];
     if (warp == 0 && i < N) {
         q[base + i] = qs[i];
         p[base + i] = vs[cb * NS * 32 + i];
@@ -322,15 +369,15 @@ fp64_small_kernel(GleF64 g, int N, int Np, const double* __restrict__ M, double*
 }
 
 cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
-                              uint32_t kappa0, int64_t iters, double* xi, cudaStream_t st) {
+                              uint32_t kappa0, int64_t iters, int prologue, double* xi,
+                              cudaStream_t st) {
     if (iters <= 0) return cudaSuccess;
-    const int64_t calls = (2 * (ns + 1) + 3) / 4;                  // per replica pair
-    const int64_t total = iters * (R / 2 + 1) * calls * N;
+    const int64_t total = iters * (R / 2 + 1) * N;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
 #define FTH_F64N_CASE(NSV)                                                                  \
     case NSV:                                                                               \
-        fp64_noise_kernel<NSV><<<grid, 256, 0, st>>>(g.key0, g.key1, g.roff, (int)N, (int)Np, \
-                                                     (int)R, kappa0, (int)iters, xi);       \
+        fp64_noise_kernel<NSV><<<grid, 256, 0, st>>>(g, (int)N, (int)Np, (int)R, kappa0,    \
+                                                     (int)iters, prologue, xi);             \
         break;
     switch (ns) {
         FTH_F64N_CASE(1)
@@ -344,6 +391,10 @@ cudaError_t launch_fp64_noise(int ns, const GleF64& g, int64_t N, int64_t Np, in
     return cudaGetLastError();
 }
 
+// Warps per replica of the N <= 32 kernel: eight split the force columns four ways finer
+// and give each of the NS + 1 O outputs its own warp.
+constexpr int kFp64Warps = 8;
+
 cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, int64_t R,
                               const double* M, double* q, double* p, double* s,
                               const double* noise, int64_t nsteps, int primed_in, int observable,
@@ -353,14 +404,15 @@ cudaError_t launch_fp64_dense(int ns, const GleF64& g, int64_t N, int64_t Np, in
     const int iters = (int)nsteps + prologue;
     if (iters <= 0) return cudaSuccess;
     constexpr size_t kBudget = 200 * 1024;
-    const size_t small_bytes = sizeof(double) * (32 * 6 + 2 * (size_t)ns * 32 + 32 * 32) +
+    const size_t small_bytes = sizeof(double) * (32 * (2 + kFp64Warps) + 2 * (size_t)ns * 32 +
+                                                 32 * 32) +
                                (size_t)npairs * 16;
     if (N <= 32 && small_bytes <= kBudget) {
 #define FTH_F64S_CASE(NSV)                                                                  \
     case NSV:                                                                               \
-        cudaFuncSetAttribute(fp64_small_kernel<NSV>,                                        \
+        cudaFuncSetAttribute(fp64_small_kernel<NSV, kFp64Warps>,                            \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);    \
-        fp64_small_kernel<NSV><<<(unsigned)R, 128, small_bytes, st>>>(                      \
+        fp64_small_kernel<NSV, kFp64Warps><<<(unsigned)R, kFp64Warps * 32, small_bytes, st>>>( \
             g, (int)N, (int)Np, M, q, p, s, noise, iters, prologue, observable, pairs,      \
             (int)npairs, partial, (int)acc_from);                                           \
         break;
