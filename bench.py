@@ -1093,7 +1093,11 @@ def main():
     f.profile(False)
     peaks, peak_kind = _peaks()
     n64 = prof.get("fp64_dense", (0.0, 1))[1]
-    info = {"stack_cols": (2048 // wl.R) * wl.R if wl.track == "all" else 4 * wl.R,
+    # staged columns per accumulation pass (the library's default stack): 4096 BF16 columns
+    # on the tensor-core paths, 2048 FP32 on the FFMA path, 4 samples for element lists
+    tc_all = wl.track == "all" and wl.precision in ("tf32", "bf16x3")
+    cols = 4096 if tc_all else 2048
+    info = {"stack_cols": (cols // wl.R) * wl.R if wl.track == "all" else 4 * wl.R,
             "steps_per_launch": prof_steps / max(n64, 1)}
     roof = roofline(prof, wl, info, peaks, peak_kind)
 
@@ -1142,7 +1146,8 @@ def main():
         line["config"]["l2"] = (
             "per-step working set > L2: M %d MB + state %d MB + staged samples %d MB + partial "
             "sums %d MB; steps back to back" % (
-                wl.M32.nbytes >> 20, (8 * wl.n * wl.R * 4) >> 20, (wl.n * sc * 4) >> 20,
+                wl.M32.nbytes >> 20, (8 * wl.n * wl.R * 4) >> 20,
+                (wl.n * sc * (2 if tc_all else 4)) >> 20,
                 ((wl.n // 128) * (wl.n // 128 + 1) // 2 * 128 * 128 * 4) >> 20))
     elif wl.name == "lattice64":
         line["config"]["l2"] = "state 805 MB per step > L2 (129 MB); steps back to back"
