@@ -118,6 +118,28 @@ def test_accumulation_parity_fp32(track):
     assert info["blocks"] == o.nblocks == (333 - 30) // 50
 
 
+@pytest.mark.parametrize("R,stack", [(32, 4), (64, 4), (64, 8), (64, 16), (64, 3)])
+def test_accumulation_parity_row_grouped_pairs(R, stack):
+    # CSR lattice with diagonal + nearest-neighbour pairs: the row-grouped pass (a warp holds
+    # row i's staged samples and streams its partners) for 128-, 256-, 512- and 1024-column
+    # stacks (a block of 40 samples also ends in shorter stacks), and a 3-sample stack (192
+    # columns: the ungrouped pass), against the oracle on the same noise
+    L = 6
+    n = L ** 3
+    rowptr, col, val = syn.lattice_csr(L, seed=61)
+    a, c = syn.random_gle(4, seed=62, rate=3.0)
+    pairs = np.concatenate([syn.diag_pairs(n), syn.lattice_nn_pairs(L)])
+    g, o = make_pair(csr=(rowptr, col, val, n), a_p=a, c_p=c, dt=0.1 / np.sqrt(14.5), R=R,
+                     seed=63, pairs=pairs, burnin=10, block=40, stack=stack)
+    g.run(333)
+    o.run(333)
+    vals_o, errs_o = o.elements()
+    vals_g, errs_g = g.elements(o.pairs)
+    scale = np.max(np.abs(vals_o))
+    assert np.max(np.abs(vals_g - vals_o)) <= 1e-4 * scale
+    assert np.allclose(errs_g, errs_o, rtol=1e-2, atol=1e-4 * scale)
+
+
 def test_accumulation_parity_fp64_all():
     n, R = 24, 6
     a, c = syn.random_gle(4, seed=16, rate=3.0)
