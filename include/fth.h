@@ -111,7 +111,9 @@ typedef struct {
     int track;              /* enum fth_track                                             */
     const int64_t* pairs;   /* LIST: host array of 2*npairs indices (i, j)                */
     int64_t npairs;
-    int64_t stack;          /* samples staged before one accumulation pass (0 = auto)     */
+    int64_t stack;          /* samples staged before one accumulation pass (0 = auto: 4096
+                             * BF16 columns / Rp on the tensor-core all-elements paths, 2048 /
+                             * Rp on the FFMA one, 4 for element lists)                   */
     void* stream;           /* cudaStream_t                                               */
     int64_t replica_offset; /* global index of replica 0 in the noise counter: a run split
                                across processes with offsets 0, R, 2R, ... draws exactly the

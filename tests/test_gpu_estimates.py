@@ -179,8 +179,8 @@ def test_full_size_dense_fp32_sampled():
 
 
 def test_full_size_dense_tf32_accumulators_sampled():
-    """N = 4096, R = 256, TF32 force and every element accumulated (tcgen05 SYRK over
-    stacks of 8 samples): three stacked passes and three blocks, read back on a sample
+    """N = 4096, R = 256, TF32 force and every element accumulated (tcgen05 SYRK over the
+    staged samples, one pass per block of 8 here): three passes and three blocks, read back on a sample
     of 4096 elements.  With A_p = C_p = 0 the dynamics is noise-free velocity Verlet and
     the samples of q follow in FP64 from the same start, staged in BF16 (round to nearest)
     as the accumulation pass reads them; bound 2^-9 of the products' scale (TF32 force,
