@@ -621,8 +621,9 @@ tc_syrk_wide_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ til
 // 512 TMEM columns) share each B slice, so a CTA takes 64 KiB of operands per K slice for
 // twice the MMAs of the 128 x 256 form (a third fewer operand bytes per flop).  On the
 // diagonal A and B are the same rows and one load serves both.  Needs an even number of
-// 128-row blocks.  CTA c takes blocks c, c + G, c + 2G ... (G = the number of blocks when
-// they fit one wave).  Warp 4 lane 0 issues the copies (running ahead into the next block
+// 128-row blocks.  BF16 operands (kind::f16, 64 K per 128-byte slice).  CTA c takes blocks
+// c, c + G, c + 2G ... (G = min(blocks, SMs): one CTA fits an SM).  Warp 4 lane 0 issues the
+// copies (running ahead into the next block
 // while the accumulator drains), warp 5 lane 0 the MMAs, warps 0..3 (one TMEM lane
 // quadrant each) drain the accumulator: 128-row x 32-column boxes staged in shared memory
 // (SWIZZLE_128B, OUTB buffers) are added into the FP32 partial tiles in L2 by TMA tensor
