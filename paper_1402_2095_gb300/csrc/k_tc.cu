@@ -957,7 +957,7 @@ static cudaError_t launch_splitk(const TcForce* tf, float* MQ, int64_t ldf, uint
 
 
 constexpr int kPairStages = 3;
-constexpr int kPairKSplit = 8;
+constexpr int kPairKSplit = 9;
 
 template <int KS>
 static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t st) {
@@ -982,9 +982,9 @@ static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t
                               err, tf->stall_ns);
 }
 
-// K split 8 fills the SMs from N = 4096 up (16 row pairs x 8 = 128 CTAs); smaller problems
-// split K 16 ways so they still start about as many CTAs (each CTA's partial tile, and so
-// its epilogue, is the same size either way).
+// K split 9 fills 144 of the 152 SMs at N = 4096 (16 row pairs x 9; 8 ways left 24 idle);
+// smaller problems split K 18 ways so they still start about as many CTAs (each CTA's
+// partial tile, and so its epilogue, is the same size either way).
 static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st) {
     return tf->Np / 256 * kPairKSplit >= 96 ? launch_pair_ks<kPairKSplit>(tf, err, st)
                                             : launch_pair_ks<2 * kPairKSplit>(tf, err, st);
