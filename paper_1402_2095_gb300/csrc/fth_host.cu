@@ -314,7 +314,8 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
         L->off_q0 = c.take((size_t)Np * Rp * 4);
         L->off_p = c.take((size_t)Np * Rp * 4);
         L->off_s = c.take((size_t)std::max(nsub, 1) * Np * Rp * 4);
-        L->off_MQ = c.take((size_t)Np * Rp * 4);
+        const int planes = tc ? 1 : sgemm_force_planes(Rp);      // FP32: K shares summed later
+        L->off_MQ = c.take((size_t)planes * Np * Rp * 4);
         if (tc) {
             L->off_ophi = c.take((size_t)Rp * Np * esz);
             if (o->precision == FTH_PREC_BF16X3) L->off_oplo = c.take((size_t)Rp * Np * esz);
@@ -627,8 +628,9 @@ fth_status flush(fth_ctx* c) {
     return FTH_OK;
 }
 
-// The force arrives as one plane (the split-K kernel reduces its K shares on chip).
-int mq_planes(const fth_ctx*) { return 1; }
+// The tensor-core forces arrive as one plane (their K shares are reduced on chip or in
+// L2); the FP32 force writes one plane per K share.
+int mq_planes(const fth_ctx* c) { return is_tc(c) ? 1 : sgemm_force_planes(c->L.Rp); }
 
 // kZeroMQ when the force adds its partial sums into MQ (the element-wise step zeroes it).
 int zero_mq(const fth_ctx* c) { return c->tcf && tc_force_accumulates(c->tcf) ? kZeroMQ : 0; }

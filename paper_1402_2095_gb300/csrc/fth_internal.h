@@ -85,6 +85,8 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
                              cudaStream_t st);
 
+// Planes of MQ the FP32 force writes (its K shares; the element-wise step sums them).
+int sgemm_force_planes(int64_t Rp);
 cudaError_t launch_sgemm_force(const float* M, int64_t ldm, const float* q, int64_t Rp,
                                float* MQ, int64_t N, cudaStream_t st);
 

@@ -217,13 +217,16 @@ cudaError_t launch_pair_accum_rows(const float* ps, int64_t ps_ld, int64_t ncols
 
 // -------------------------------------------------------------- FP32 FFMA SYRK
 // tiles[t(I,J)][a][b] += sum_c ps[I*128+a][c] ps[J*128+b][c] for the upper tiles I <= J.
-// 256 threads, 8 x 8 outputs each, BK = 8.
-__global__ void __launch_bounds__(256)
+// 256 threads as 16 x 16, each 8 x 8 outputs at rows {4ty .. 4ty + 3, 64 + 4ty ..} and
+// columns {4tx .., 64 + 4tx ..} (the four float4 shared-memory reads of a k step are
+// contiguous across the warp: no bank conflicts); BK = 8; the next k tile goes through
+// registers while this one is multiplied (double-buffered shared memory).
+__global__ void __launch_bounds__(256, 2)
 syrk_fp32_kernel(const float* __restrict__ ps, int64_t ps_ld, int64_t ncols, int nbt,
                  float* __restrict__ tiles) {
     constexpr int BK = 8;
-    __shared__ __align__(16) float As[BK][kTile];
-    __shared__ __align__(16) float Bs[BK][kTile];
+    __shared__ __align__(16) float As[2][BK][kTile];
+    __shared__ __align__(16) float Bs[2][BK][kTile];
     int t = blockIdx.x, I = 0;
     while (t >= nbt - I) {
         t -= nbt - I;
@@ -231,39 +234,70 @@ syrk_fp32_kernel(const float* __restrict__ ps, int64_t ps_ld, int64_t ncols, int
     }
     const int J = I + t;
     const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
-    const float* A = ps + (int64_t)I * kTile * ps_ld;
-    const float* B = ps + (int64_t)J * kTile * ps_ld;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int lr = tid >> 1, lk = (tid & 1) * 4;        // loader: row, first of 4 k
+    const float* A = ps + ((int64_t)I * kTile + lr) * ps_ld + lk;
+    const float* B = ps + ((int64_t)J * kTile + lr) * ps_ld + lk;
     float acc[8][8] = {};
-    const int lr = tid / 2, lk = (tid % 2) * 4;
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+    if (lk < ncols) {
+        ra = *reinterpret_cast<const float4*>(A);
+        rb = *reinterpret_cast<const float4*>(B);
+    }
+    auto stage = [&](int buf) {
+        As[buf][lk + 0][lr] = ra.x;
+        As[buf][lk + 1][lr] = ra.y;
+        As[buf][lk + 2][lr] = ra.z;
+        As[buf][lk + 3][lr] = ra.w;
+        Bs[buf][lk + 0][lr] = rb.x;
+        Bs[buf][lk + 1][lr] = rb.y;
+        Bs[buf][lk + 2][lr] = rb.z;
+        Bs[buf][lk + 3][lr] = rb.w;
+    };
+    stage(0);
+    __syncthreads();
+    int cur = 0;
     for (int64_t k0 = 0; k0 < ncols; k0 += BK) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (k0 + lk < ncols) {
-            a = *reinterpret_cast<const float4*>(A + (int64_t)lr * ps_ld + k0 + lk);
-            b = *reinterpret_cast<const float4*>(B + (int64_t)lr * ps_ld + k0 + lk);
+        const bool more = k0 + BK < ncols;
+        if (more) {
+            ra = rb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + BK + lk < ncols) {
+                ra = *reinterpret_cast<const float4*>(A + k0 + BK);
+                rb = *reinterpret_cast<const float4*>(B + k0 + BK);
+            }
         }
-        As[lk + 0][lr] = a.x; As[lk + 1][lr] = a.y; As[lk + 2][lr] = a.z; As[lk + 3][lr] = a.w;
-        Bs[lk + 0][lr] = b.x; Bs[lk + 1][lr] = b.y; Bs[lk + 2][lr] = b.z; Bs[lk + 3][lr] = b.w;
-        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float av[8], bv[8];
-#pragma unroll
-            for (int x = 0; x < 8; ++x) av[x] = As[kk][ty * 8 + x];
-#pragma unroll
-            for (int y = 0; y < 8; ++y) bv[y] = Bs[kk][tx * 8 + y];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int x = 0; x < 8; ++x)
 #pragma unroll
                 for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
         }
+        if (more) stage(cur ^ 1);
         __syncthreads();
+        cur ^= 1;
     }
     float* out = tiles + (int64_t)blockIdx.x * kTile * kTile;
 #pragma unroll
-    for (int x = 0; x < 8; ++x)
+    for (int x = 0; x < 8; ++x) {
+        const int r = x < 4 ? ty * 4 + x : 64 + ty * 4 + x - 4;
 #pragma unroll
-        for (int y = 0; y < 8; ++y) out[(ty * 8 + x) * kTile + tx * 8 + y] += acc[x][y];
+        for (int h = 0; h < 2; ++h) {
+            float4* o = reinterpret_cast<float4*>(out + r * kTile + h * 64 + tx * 4);
+            float4 v = *o;
+            v.x += acc[x][4 * h];
+            v.y += acc[x][4 * h + 1];
+            v.z += acc[x][4 * h + 2];
+            v.w += acc[x][4 * h + 3];
+            *o = v;
+        }
+    }
 }
 
 cudaError_t launch_syrk_fp32(const float* ps, int64_t ps_ld, int64_t ncols, int64_t Np,
