@@ -88,7 +88,8 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
         for (int j = blockIdx.x; j < nitems && ok; j += gridDim.x) {
             const PoolForceItem it = items[j];
             const PoolDesc& d = desc[it.problem];
-            const int nk = d.np / KS;
+            const int nks = d.np / KS;              // K slices per row block in the layout
+            const int nk = (d.n + KS - 1) / KS;     // those past n are all zero padding
             const int J = it.rb, nb = d.np >> 7;
             const bool sym = KIND == 2 && d.sym;
             for (int kb = 0; kb < nk && ok; ++kb, ++c) {
@@ -110,7 +111,7 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
                         mn = true;
                     }
                 } else {
-                    a_off = ((size_t)J * nk + kb) * C::kABytes;
+                    a_off = ((size_t)J * nks + kb) * C::kABytes;
                 }
                 const int nplanes = KIND == 2 ? 2 : 1;
                 for (int pl = 0; pl < nplanes; ++pl) {
@@ -145,7 +146,7 @@ pool_force_kernel(const PoolDesc* __restrict__ desc, const PoolForceItem* __rest
             fence_after_sync();
             const PoolForceItem it = items[j];
             const PoolDesc& d = desc[it.problem];
-            const int nk = d.np / KS;
+            const int nk = (d.n + KS - 1) / KS;     // K slices past n are all zero padding
             const bool sym = KIND == 2 && d.sym;
             const uint32_t acc_t = tmem + (uint32_t)(a * RN);
             for (int kb = 0; kb < nk; ++kb, ++c) {
