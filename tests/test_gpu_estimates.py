@@ -272,17 +272,18 @@ def test_nonfinite_state_reaches_the_flush(which):
     assert ex.value.status == 7, name
 
 
-@pytest.mark.parametrize("R", [64, 256])
-def test_device_wait_timeout_is_reported(R):
+@pytest.mark.parametrize("n,R", [(300, 64), (300, 256), (512, 256)])
+def test_device_wait_timeout_is_reported(n, R):
     """fth_test_stall: the force launches issue no copies, so the main-loop waits of
     every CTA give up after 1 ms; the call reports FTH_E_TIMEOUT and the CUDA context
     stays usable (a new context afterwards runs and matches the oracle).  R = 64 takes
-    the column-tiled kernel, R = 256 the split-K cluster kernel."""
+    the column-tiled kernel, n = 300 with R = 256 the split-K cluster kernel, n = 512
+    with R = 256 the row-pair kernel with L2 reduce-adds."""
     from paper_1402_2095_gb300 import FTH, FthError
-    M, _, _ = syn.dense_spd(300, 1.0, 100.0, seed=311)
+    M, _, _ = syn.dense_spd(n, 1.0, 100.0, seed=311)
     M32 = M.astype(np.float32)
     a, c = syn.random_gle(4, seed=312, rate=3.0)
-    pairs = syn.diag_pairs(300)[:8]
+    pairs = syn.diag_pairs(n)[:8]
     f = FTH(M=M32, a_p=a, c_p=c, dt=0.01, replicas=R, seed=6, precision="tf32", pairs=pairs,
             block=4)
     f.run(3)

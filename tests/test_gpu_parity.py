@@ -89,7 +89,8 @@ def _force_through_prologue(M, q0, precision, dt=0.01):
                                              ("bf16x3", 2.0 ** -15)])
 @pytest.mark.parametrize("n,R", [(300, 70), (128, 64), (77, 5),     # column-tiled kernel
                                  (300, 200), (77, 250), (640, 256),   # split-K cluster kernel
-                                 (512, 200), (1000, 256), (1024, 140)])  # several row blocks
+                                 (512, 200), (1000, 256), (1024, 140),   # several row blocks
+                                 (2048, 256), (4096, 200)])   # K shares longer than the ring
 def test_force_gemm(precision, bound, n, R):
     M = _dense(n, seed=21).astype(np.float32).astype(np.float64)
     q0 = syn.gaussian_state((R, n), seed=22)
