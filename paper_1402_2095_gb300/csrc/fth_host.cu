@@ -543,41 +543,52 @@ fth_status claim_stack(fth_ctx* c) {
     return FTH_OK;
 }
 
-// One accumulation pass over the filled stack, on the side stream; the other stack
-// takes the next samples meanwhile.
+// The stream of the accumulation passes and block flushes.  The tensor-core pass over
+// all elements runs in line on the caller's stream: beside the next steps its CTAs held
+// SMs the force needed, which cost more than the pass itself.  The other passes run on
+// the side stream, beside the next steps.
+cudaStream_t acc_stream(const fth_ctx* c) {
+    return c->L.track == FTH_TRACK_ALL && is_tc(c) ? c->stream : c->side;
+}
+
+// One accumulation pass over the filled stack; the other stack takes the next samples
+// meanwhile.
 fth_status accumulate(fth_ctx* c) {
     const Layout& L = c->L;
     if (c->nfill == 0) return FTH_OK;
     const int64_t ncols = c->nfill * L.Rp;
     const int b = c->psi;
-    FTH_CK(cudaEventRecord(c->ev_filled[b], c->stream), "record filled");
-    FTH_CK(cudaStreamWaitEvent(c->side, c->ev_filled[b], 0), "side wait");
-    c->side_used = true;
+    const cudaStream_t as = acc_stream(c);
+    if (as != c->stream) {
+        FTH_CK(cudaEventRecord(c->ev_filled[b], c->stream), "record filled");
+        FTH_CK(cudaStreamWaitEvent(as, c->ev_filled[b], 0), "side wait");
+        c->side_used = true;
+    }
     {
         ProfScope ps(c, L.track == FTH_TRACK_ALL ? (is_tc(c) ? FTH_K_SYRK_TC : FTH_K_SYRK_FP32)
                                                  : FTH_K_PAIR_ACCUM,
-                     c->side);
+                     as);
         if (L.track == FTH_TRACK_ALL) {
             if (is_tc(c)) {
                 FTH_CK(tc_syrk_run(b ? c->tcs1 : c->tcs, ncols, static_cast<float*>(c->partial),
-                                   c->err, c->side),
+                                   c->err, as),
                        "tc syrk");
             } else {
                 FTH_CK(launch_syrk_fp32(c->psb[b], L.ps_ld, ncols, L.Np,
-                                        static_cast<float*>(c->partial), c->side),
+                                        static_cast<float*>(c->partial), as),
                        "syrk");
             }
         } else if (c->prow && pair_accum_rows_supported(ncols)) {
             FTH_CK(launch_pair_accum_rows(c->psb[b], L.ps_ld, ncols, c->prow, c->pcol, c->pe, L.N,
-                                          static_cast<float*>(c->partial), c->side),
+                                          static_cast<float*>(c->partial), as),
                    "pair accumulate (rows)");
         } else {
             FTH_CK(launch_pair_accum(c->psb[b], L.ps_ld, ncols, c->pairs, L.ntracked,
-                                     static_cast<float*>(c->partial), c->side),
+                                     static_cast<float*>(c->partial), as),
                    "pair accumulate");
         }
     }
-    FTH_CK(cudaEventRecord(c->ev_free[b], c->side), "record free");
+    FTH_CK(cudaEventRecord(c->ev_free[b], as), "record free");
     c->free_pending[b] = true;
     ++c->launches;
     c->nfill = 0;
@@ -601,7 +612,7 @@ fth_status flush(fth_ctx* c) {
     // functionals first: they read the block's partial sums before the flush clears them
     for (auto& f : c->funcs) {
         const bool p64 = L.path == kPathDense64;
-        cudaStream_t st = p64 ? c->stream : c->side;
+        cudaStream_t st = p64 ? c->stream : acc_stream(c);
         FTH_CK(launch_functional_block(p64 ? nullptr : static_cast<const float*>(c->partial),
                                        p64 ? static_cast<const double*>(c->partial) : nullptr,
                                        L.R, L.count, f.idx, f.w, f.nterms, inv, nb, f.acc, c->err,
@@ -615,12 +626,13 @@ fth_status flush(fth_ctx* c) {
                               L.count, inv, nb, c->err, c->stream),
                "flush64");
     } else {
-        // after the block's last accumulation pass, on the same (side) stream
-        ProfScope ps(c, FTH_K_FLUSH, c->side);
+        // after the block's last accumulation pass, on the same stream
+        const cudaStream_t as = acc_stream(c);
+        ProfScope ps(c, FTH_K_FLUSH, as);
         FTH_CK(launch_flush(static_cast<float*>(c->partial), c->mean, c->m2, L.count, inv, nb,
-                            c->err, c->side),
+                            c->err, as),
                "flush");
-        c->side_used = true;
+        if (as != c->stream) c->side_used = true;
     }
     ++c->launches;
     ++c->nblocks;

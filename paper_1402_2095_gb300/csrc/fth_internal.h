@@ -28,14 +28,26 @@ struct GleF32 {
     uint32_t key0, key1;
     uint32_t roff;   // replica offset in the noise counter
     uint32_t rk[20]; // Philox round keys: key + j * (0x9E3779B9, 0xBB67AE85), j = 0..9
+    // The constants of the two-replica update (gle_fused2), each duplicated into both
+    // lanes: a packed FP32 instruction reads such a pair as one 64-bit operand.
+    float2 D2x2[kMaxNs * kMaxNs];
+    float2 Lx2[kMaxNs1 * kMaxNs1];
+    float2 T0x2[kMaxNs];   // row 0 of D = T - I
+    float2 mhdt2, dt2;     // -dt/2 and dt
 };
 
-// Fills g.rk from g.key0, g.key1.
+// Fills g.rk from g.key0, g.key1, and the duplicated pairs from D2, L, T, hdt and dt
+// (call once those are set).
 inline void set_round_keys(GleF32& g) {
     for (int j = 0; j < 10; ++j) {
         g.rk[2 * j] = g.key0 + (uint32_t)j * 0x9E3779B9u;
         g.rk[2 * j + 1] = g.key1 + (uint32_t)j * 0xBB67AE85u;
     }
+    for (int k = 0; k < kMaxNs * kMaxNs; ++k) g.D2x2[k] = make_float2(g.D2[k], g.D2[k]);
+    for (int k = 0; k < kMaxNs1 * kMaxNs1; ++k) g.Lx2[k] = make_float2(g.L[k], g.L[k]);
+    for (int k = 0; k < kMaxNs; ++k) g.T0x2[k] = make_float2(g.T[k], g.T[k]);
+    g.mhdt2 = make_float2(-g.hdt, -g.hdt);
+    g.dt2 = make_float2(g.dt, g.dt);
 }
 
 struct GleF64 {

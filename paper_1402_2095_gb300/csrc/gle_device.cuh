@@ -206,4 +206,88 @@ __device__ __forceinline__ void gle_fused(float& q, float (&v)[NS], float mq, co
     }
 }
 
+// The steady-state update (end and start) of two replicas at once, one in each lane of
+// float2 registers: the same sequence of roundings as gle_fused, issued as packed FP32
+// instructions (each lane of fma.rn.f32x2 rounds as fmaf does), so both lanes equal
+// gle_fused's results bit for bit in half the floating-point instructions.
+template <int NS>
+__device__ __forceinline__ void o_joint2(float2 (&v)[NS], const GleF32& g,
+                                         const float2 (&zeta)[NS + 1], float2& pmid) {
+    float2 inc = __fmul2_rn(g.Lx2[0], zeta[0]);
+#pragma unroll
+    for (int b = 0; b < NS; ++b) inc = __ffma2_rn(g.T0x2[b], v[b], inc);
+    pmid = __fadd2_rn(v[0], inc);
+    float2 out[NS];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < NS; ++b) acc = __ffma2_rn(g.D2x2[a * kMaxNs + b], v[b], acc);
+#pragma unroll
+        for (int b = 0; b <= a + 1; ++b) acc = __ffma2_rn(g.Lx2[(a + 1) * kMaxNs1 + b], zeta[b], acc);
+        out[a] = __fadd2_rn(v[a], acc);
+    }
+#pragma unroll
+    for (int a = 0; a < NS; ++a) v[a] = out[a];
+}
+
+template <int NS>
+__device__ __forceinline__ void gle_fused2(float2& q, float2 (&v)[NS], float2 mq, const GleF32& g,
+                                           const float2 (&zeta)[NS + 1], int observable,
+                                           float2& sample) {
+    v[0] = __ffma2_rn(g.mhdt2, mq, v[0]);
+    float2 pmid;
+    o_joint2<NS>(v, g, zeta, pmid);
+    sample = observable ? q : pmid;
+    v[0] = __ffma2_rn(g.mhdt2, mq, v[0]);
+    q = __ffma2_rn(g.dt2, v[0], q);
+}
+
+// One thread's four consecutive replicas r0 .. r0 + 3 of dof i, held as float4 (q, the
+// NS momentum planes, mq): two Philox pair streams; in the steady state a pair whose
+// replicas are both below R takes the packed update, any other replica gle_fused.
+template <int NS>
+__device__ __forceinline__ void gle_quad(float4& q4, float4 (&v4)[NS], const float4& mq4,
+                                         const GleF32& g, uint32_t kappa, uint32_t i, int r0,
+                                         int R, int flags, int observable, float (&samp)[4]) {
+    float* qa = reinterpret_cast<float*>(&q4);
+    const float* mqa = reinterpret_cast<const float*>(&mq4);
+#pragma unroll
+    for (int e = 0; e < 4; e += 2) {
+        if (r0 + e >= R) continue;
+        float xa[NS + 1], xb[NS + 1];
+        gle_normals_two<NS>(kappa, i, (uint32_t)(r0 + e) + g.roff, g.rk, xa, xb);
+        if ((flags & kDoEnd) && (flags & kDoStart) && r0 + e + 1 < R) {
+            float2 zeta[NS + 1];
+#pragma unroll
+            for (int k = 0; k <= NS; ++k) zeta[k] = make_float2(xa[k], xb[k]);
+            float2 v[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float2*>(&v4[a])[e >> 1];
+            float2 q = reinterpret_cast<float2*>(&q4)[e >> 1];
+            float2 sm;
+            gle_fused2<NS>(q, v, reinterpret_cast<const float2*>(&mq4)[e >> 1], g, zeta,
+                           observable, sm);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) reinterpret_cast<float2*>(&v4[a])[e >> 1] = v[a];
+            reinterpret_cast<float2*>(&q4)[e >> 1] = q;
+            samp[e] = sm.x;
+            samp[e + 1] = sm.y;
+            continue;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ee = e + h;
+            if (r0 + ee >= R) continue;
+            float v[NS];
+#pragma unroll
+            for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[ee];
+            if (h == 0) gle_fused<NS>(qa[ee], v, mqa[ee], g, xa, flags, observable, samp[ee]);
+            else gle_fused<NS>(qa[ee], v, mqa[ee], g, xb, flags, observable, samp[ee]);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[ee] = v[a];
+        }
+    }
+}
+
 }  // namespace fth

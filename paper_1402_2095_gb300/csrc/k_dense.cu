@@ -63,28 +63,10 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_
 #pragma unroll
         for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
 
-        float* qa = reinterpret_cast<float*>(&q4);
-        const float* mqa = reinterpret_cast<const float*>(&mq4);
+        const float* qa = reinterpret_cast<const float*>(&q4);
         float samp[4] = {0.f, 0.f, 0.f, 0.f};
         // replicas two at a time: one pair stream of normals serves both
-#pragma unroll
-        for (int e = 0; e < 4; e += 2) {
-            if (r0 + e >= R) continue;
-            float xa[NS + 1], xb[NS + 1];
-            gle_normals_two<NS>(kappa, (uint32_t)i, (uint32_t)(r0 + e) + g.roff, g.rk, xa, xb);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int ee = e + h;
-                if (r0 + ee >= R) continue;
-                float v[NS];
-#pragma unroll
-                for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float*>(&v4[a])[ee];
-                if (h == 0) gle_fused<NS>(qa[ee], v, mqa[ee], g, xa, flags, observable, samp[ee]);
-                else gle_fused<NS>(qa[ee], v, mqa[ee], g, xb, flags, observable, samp[ee]);
-#pragma unroll
-                for (int a = 0; a < NS; ++a) reinterpret_cast<float*>(&v4[a])[ee] = v[a];
-            }
-        }
+        gle_quad<NS>(q4, v4, mq4, g, kappa, (uint32_t)i, r0, R, flags, observable, samp);
         *reinterpret_cast<float4*>(q + off) = q4;
         *reinterpret_cast<float4*>(p + off) = v4[0];
 #pragma unroll

@@ -354,6 +354,27 @@ __device__ __forceinline__ void pool_gle_vec(const PoolGleShared& c, const GleF3
         for (int e = 0; e < NE; e += 2) {
             float xa[NS + 1], xb[NS + 1];
             gle_normals_two<NS>(c.kappa, (uint32_t)i, (uint32_t)(r0 + e) + c.roff, c.rk, xa, xb);
+            if ((c.flags & kDoEnd) && (c.flags & kDoStart)) {
+                // steady state: both replicas in the lanes of packed FP32 instructions
+                float2 zeta[NS + 1];
+#pragma unroll
+                for (int k = 0; k <= NS; ++k) zeta[k] = make_float2(xa[k], xb[k]);
+                float2 v[NS];
+#pragma unroll
+                for (int a = 0; a < NS; ++a) v[a] = reinterpret_cast<float2*>(&v4[a])[e >> 1];
+                float2 q = reinterpret_cast<float2*>(&q4)[e >> 1];
+                float2 sm;
+                gle_fused2<NS>(q, v, reinterpret_cast<const float2*>(&mq4)[e >> 1], gk, zeta,
+                               c.observable, sm);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) reinterpret_cast<float2*>(&v4[a])[e >> 1] = v[a];
+                reinterpret_cast<float2*>(&q4)[e >> 1] = q;
+                samp[e] = sm.x;
+                samp[e + 1] = sm.y;
+                qout[e] = q.x;
+                qout[e + 1] = q.y;
+                continue;
+            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int ee = e + h;
