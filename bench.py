@@ -268,9 +268,10 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------- roofline
-def _traffic(kernel):
-    """DRAM bytes per launch from the committed ncu capture of this kernel, or None when
-    the kernel's source has changed since the capture (hash mismatch)."""
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu capture of this kernel on this
+    workload ("name:precision"), or None when there is none or the kernel's source has
+    changed since the capture (hash mismatch)."""
     import hashlib
     try:
         lines = open(os.path.join(ROOT, "profiles", "traffic.txt")).read().splitlines()
@@ -278,13 +279,13 @@ def _traffic(kernel):
         return None
     for ln in lines:
         f = ln.split()
-        if len(f) == 4 and f[0] == kernel:
+        if len(f) == 5 and f[0] == kernel and f[1] == workload:
             try:
-                src = open(os.path.join(ROOT, f[1]), "rb").read()
+                src = open(os.path.join(ROOT, f[2]), "rb").read()
             except OSError:
                 return None
-            if hashlib.sha256(src).hexdigest()[:16] == f[2]:
-                return int(f[3])
+            if hashlib.sha256(src).hexdigest()[:16] == f[3]:
+                return int(f[4])
     return None
 
 
@@ -317,7 +318,7 @@ def roofline(prof, wl, info, peaks, peak_kind):
     out["frac"] = out["achieved"] / out["peak"]
     out["kernel"] = name
     out["launch_us"] = per_launch_s * 1e6
-    out["traffic"] = _traffic(name)
+    out["traffic"] = _traffic(name, f"{wl.name}:{wl.precision}")
     total = sum(x[0] for x in prof.values())
     out["share"] = {k: round(v[0] / total, 4) for k, v in prof.items()}
     return out
@@ -611,7 +612,7 @@ def run_ragged(args, rank, world, local):
     total = sum(v[0] for v in prof.values())
     roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peaks["hbm_gbs"],
             "peak_source": f"{peak_kind} copy", "frac": achieved / peaks["hbm_gbs"],
-            "kernel": name, "launch_us": per_launch_s * 1e6, "traffic": _traffic(name),
+            "kernel": name, "launch_us": per_launch_s * 1e6, "traffic": _traffic(name, "ragged512:bf16x3"),
             "share": {k: round(v[0] / total, 4) for k, v in prof.items()}}
     pool.close()
     del pool

@@ -13,6 +13,8 @@ bench = pytest.importorskip("bench")
 
 KNOWN = {"force_tc", "syrk_tc", "gle_dense", "csr_step", "pair_accum", "pool_force", "pool_gle",
          "pool_accum", "fp64_dense"}
+WORKLOADS = {"dense4096", "small_fp64", "lattice64", "ragged512", "m1", "m2"}
+PRECISIONS = {"fp32", "tf32", "bf16x3", "fp64"}
 
 
 def test_traffic_table_format():
@@ -20,9 +22,11 @@ def test_traffic_table_format():
     rows = [ln.split() for ln in lines if ln.strip() and not ln.startswith("#")]
     assert rows
     for f in rows:
-        assert len(f) == 4, f
-        kernel, src, digest, nbytes = f
+        assert len(f) == 5, f
+        kernel, workload, src, digest, nbytes = f
         assert kernel in KNOWN, kernel
+        name, precision = workload.split(":")
+        assert name in WORKLOADS and precision in PRECISIONS, workload
         assert os.path.exists(os.path.join(ROOT, src)), src
         assert re.fullmatch(r"[0-9a-f]{16}", digest), digest
         assert int(nbytes) > 0
@@ -34,16 +38,20 @@ def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
     digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.txt").write_text(
-        f"# header\nforce_tc  k.cu  {digest}  12345\ngle_dense  k.cu  0000000000000000  7\n")
+        f"# header\nforce_tc  dense4096:tf32  k.cu  {digest}  12345\n"
+        "gle_dense  dense4096:tf32  k.cu  0000000000000000  7\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic("force_tc") == 12345
-    assert bench._traffic("gle_dense") is None          # stale capture: source changed
-    assert bench._traffic("csr_step") is None           # never captured
+    assert bench._traffic("force_tc", "dense4096:tf32") == 12345
+    assert bench._traffic("force_tc", "m2:tf32") is None      # captured on another workload
+    assert bench._traffic("force_tc", "dense4096:bf16x3") is None
+    assert bench._traffic("gle_dense", "dense4096:tf32") is None   # stale: source changed
+    assert bench._traffic("csr_step", "lattice64:fp32") is None    # never captured
     src.write_text("kernel source v2\n")
-    assert bench._traffic("force_tc") is None
+    assert bench._traffic("force_tc", "dense4096:tf32") is None
 
 
 class _Wl:
+    name = "dense4096"
     precision = "tf32"
 
     def work(self, cls, info):
