@@ -275,6 +275,14 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
                        int N, int Rp, int nslices_total, uint32_t* err, uint64_t stall_ns) {
     constexpr int LDS = BN + 4;                 // padded row of the staged partial
     static_assert(STAGES * TcCfg<KIND, BN>::kStageBytes >= 128 * LDS * 4, "stage space");
+    if (threadIdx.x == 64) {
+        prefetch_tensormap(&maps.a_hi);
+        prefetch_tensormap(&maps.b_hi);
+        if (KIND == 2) {
+            prefetch_tensormap(&maps.a_lo);
+            prefetch_tensormap(&maps.b_lo);
+        }
+    }
     uint8_t* stages;
     uint64_t *full, *empty, *done;
     uint32_t tmem;
@@ -361,6 +369,11 @@ tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant_
     uint64_t* done = full + 2 * STAGES;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2 * STAGES + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 64) {
+        prefetch_tensormap(&maps.a_hi);
+        prefetch_tensormap(&maps.b_hi);
+        prefetch_tensormap(&mq);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
@@ -647,6 +660,11 @@ tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ C
     uint64_t* drain = tfull + 2;                // MMA completion after a timed-out wait
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tfull + 3);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 64) {
+        prefetch_tensormap(&maps.a_hi);
+        prefetch_tensormap(&maps.b_hi);
+        prefetch_tensormap(&part);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),

@@ -251,6 +251,12 @@ __device__ __forceinline__ void fence_after_sync() {
 }
 
 
+// Bring a tensor map (a __grid_constant__ kernel parameter) into the TMA unit's descriptor
+// cache ahead of its first copy, so that fetch overlaps the CTA's setup.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 // Plain bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global
 // to shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
