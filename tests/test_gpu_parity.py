@@ -72,6 +72,30 @@ def test_tensor_core_trajectory(precision, tol):
     assert _trajectory(g, o, 400, 2) <= tol
 
 
+def test_tensor_core_trajectory_row_pair_kernel():
+    """TF32 on whole row pairs (N a multiple of 256, 128 < R <= 256): the row-pair force
+    with L2 reduce-adds, each element-wise block starting once every force CTA has read
+    its q^T and its own row pair's sums have landed (the force's completion counters).
+    400 steps against the oracle on the first 16 of the 256 replicas: replicas evolve
+    independently and draw their own noise, so the oracle needs no others."""
+    from oracle.fth import OracleFTH
+    from paper_1402_2095_gb300 import FTH
+    n, R, Ro = 512, 256, 16
+    a, c = syn.random_gle(4, seed=14, rate=3.0)
+    M = _dense(n).astype(np.float32)
+    g = FTH(M=M, a_p=a, c_p=c, dt=0.01, replicas=R, seed=5, precision="tf32")
+    o = OracleFTH(M=_dense(n), a_p=a, c_p=c, dt=0.01, replicas=Ro, seed=5)
+    diff = ref = 0.0
+    for _ in range(4):
+        g.run(100)
+        o.run(100)
+        for name, r in (("q", o.q), ("p", o.p), ("s", o.s)):
+            diff = max(diff, float(np.max(np.abs(g.get_state(name)[:Ro] - r))))
+            ref = max(ref, float(np.max(np.abs(r))))
+    g.poll()
+    assert diff / ref <= 3e-2
+
+
 # ------------------------------------------------------------------ force kernels alone
 def _force_through_prologue(M, q0, precision, dt=0.01):
     """With A_p = 0 and C_p = 0 (T = I, S = 0) and p = 0, the prologue leaves
