@@ -152,8 +152,8 @@ fth_status fth_create(const fth_matrix* M, const fth_gle* gle, const fth_options
 /* Advance the dynamics by `steps` steps, taking one sample per step (the hot path:
  * force, B, O, sample, O, B, A per step, plus one accumulation pass per `stack`
  * samples and one FP64 block flush per completed block).  Asynchronous.  Each launch
- * carries per-step values that the context tracks on the host (kick index, stack slot,
- * the force's completion targets), so the launches of a call are not meant to be
+ * carries per-step values that the context tracks on the host (kick index, stack slot),
+ * so the launches of a call are not meant to be
  * captured into a CUDA graph and replayed; fth_dense_step_noalloc is the entry point for
  * capture. */
 fth_status fth_run(fth_ctx* ctx, int64_t steps);

@@ -46,7 +46,6 @@ struct Layout {
     size_t off_ps = 0, off_ps1 = 0, off_pairs = 0, off_partial = 0, off_mean = 0, off_m2 = 0;
     size_t off_prow = 0, off_pcol = 0, off_pe = 0;   // pairs grouped by row (FP32 list paths)
     size_t off_gidx = 0, off_gout = 0, off_err = 0;
-    size_t off_fsync = 0;    // ForceSync counters of the row-pair force (dense TF32)
     size_t off_xi = 0;       // FP64 path: normals of one segment
     int64_t xi_chunk = 0;    // kick indices per segment that the buffer holds
     size_t total = 0;
@@ -360,7 +359,6 @@ fth_status plan(const fth_matrix* M, const fth_gle* gle, const fth_options* o, L
     L->off_gidx = c.take((size_t)L->gcap * 8);
     L->off_gout = c.take((size_t)L->gcap * 3 * 8);
     L->off_err = c.take(256);
-    L->off_fsync = c.take(((size_t)(L->Np / 256) + 2) * 4);
     L->total = c.off;
     return FTH_OK;
 }
@@ -431,8 +429,6 @@ struct fth_ctx {
     int64_t* gidx = nullptr;
     double* gout = nullptr;
     uint32_t* err = nullptr;
-    uint32_t* fsync = nullptr;    // ForceSync words (zero at create, only grow)
-    uint32_t fgen = 0;            // row-pair force launches so far
     TcForce* tcf = nullptr;
     TcSyrk* tcs = nullptr;
     TcSyrk* tcs1 = nullptr;
@@ -526,9 +522,7 @@ fth_status force(fth_ctx* c) {
     const Layout& L = c->L;
     ProfScope ps(c, is_tc(c) ? FTH_K_FORCE_TC : FTH_K_FORCE_FP32);
     if (is_tc(c)) {
-        FTH_CK(tc_force_run(c->tcf, c->MQ, L.Rp, c->err, c->stream, c->fsync), "tc force");
-        uint32_t ctas, ks;
-        if (tc_force_sync_counts(c->tcf, &ctas, &ks)) ++c->fgen;
+        FTH_CK(tc_force_run(c->tcf, c->MQ, L.Rp, c->err, c->stream), "tc force");
     } else {
         FTH_CK(launch_sgemm_force(static_cast<const float*>(c->M), L.Np,
                                   static_cast<const float*>(c->q[0]), L.Rp, c->MQ, L.N, c->stream),
@@ -653,20 +647,6 @@ int mq_planes(const fth_ctx* c) { return is_tc(c) ? 1 : sgemm_force_planes(c->L.
 // kZeroMQ when the force adds its partial sums into MQ (the element-wise step zeroes it).
 int zero_mq(const fth_ctx* c) { return c->tcf && tc_force_accumulates(c->tcf) ? kZeroMQ : 0; }
 
-// The completion targets the element-wise step after the latest force launch waits for
-// (the row-pair force only; otherwise it waits for the whole force grid).
-ForceSync force_sync(const fth_ctx* c) {
-    ForceSync fs;
-    uint32_t ctas, ks;
-    if (c->tcf && tc_force_sync_counts(c->tcf, &ctas, &ks)) {
-        fs.words = c->fsync;
-        fs.expect_main = ctas * c->fgen;
-        fs.expect_rows = ks * c->fgen;
-        fs.err = c->err;
-    }
-    return fs;
-}
-
 void op_ptrs(fth_ctx* c, int& kind, void*& hi, void*& lo) {
     kind = kOpNone;
     hi = lo = nullptr;
@@ -692,7 +672,7 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
             ProfScope ps(c, FTH_K_GLE_DENSE);
             FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, mq_planes(c), q, p, s,
                                     (uint32_t)c->t, kDoStart | zero_mq(c), c->observable, c->ps,
-                                    L.ps_ld, 0, opk, hi, lo, L.Np, force_sync(c), c->stream),
+                                    L.ps_ld, 0, opk, hi, lo, L.Np, c->stream),
                    "gle prologue");
         }
         ++c->launches;
@@ -714,7 +694,7 @@ fth_status run_dense32(fth_ctx* c, int64_t steps) {
             ProfScope ps(c, FTH_K_GLE_DENSE);
             FTH_CK(launch_dense_gle(L.ns, c->g32, L.N, L.R, L.Rp, c->MQ, mq_planes(c), q, p, s,
                                     kappa, flags, c->observable, c->ps, L.ps_ld, c->nfill, opk,
-                                    hi, lo, L.Np, force_sync(c), c->stream),
+                                    hi, lo, L.Np, c->stream),
                    "gle step");
         }
         ++c->launches;
@@ -958,7 +938,6 @@ fth_status fth_create(const fth_matrix* Min, const fth_gle* gle, const fth_optio
     c->gidx = static_cast<int64_t*>(at(L.off_gidx));
     c->gout = static_cast<double*>(at(L.off_gout));
     c->err = static_cast<uint32_t*>(at(L.off_err));
-    c->fsync = static_cast<uint32_t*>(at(L.off_fsync));
     if (L.path == kPathCsr) {
         c->rowptr = static_cast<int32_t*>(at(L.off_rowptr));
         c->col = static_cast<int32_t*>(at(L.off_col));

@@ -88,18 +88,6 @@ enum : int { kDoEnd = 1, kDoStart = 2, kDoSample = 4, kSampleBf16 = 8, kZeroMQ =
 // Operand copies of q the element-wise kernel writes for the force GEMM.
 enum : int { kOpNone = 0, kOpTf32 = 1, kOpBf16x2 = 2 };
 
-// Completion counters of the row-pair force, read by the element-wise step launched after
-// it (a programmatic dependent launch) in place of a wait for the whole force grid: word 0
-// counts the force CTAs whose main loop has ended (they no longer read q^T), word 1 + t the
-// CTAs whose partial sums for rows 256 t .. 256 t + 255 have landed in MQ.  The counters
-// only grow (modulo 2^32); a step waits until they reach its launch's targets.
-struct ForceSync {
-    uint32_t* words = nullptr;   // nullptr: wait for the whole previous grid
-    uint32_t expect_main = 0;    // target of word 0
-    uint32_t expect_rows = 0;    // target of each word 1 + t
-    uint32_t* err = nullptr;     // device error word (a wait that runs out sets kErrTimeout)
-};
-
 // ------------------------------------------------------------------ kernels
 // Dense path, state planes [Np][Rp] FP32 (replica fastest), MQ = M q (positive).
 cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int64_t Rp,
@@ -107,7 +95,7 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
                              uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
-                             const ForceSync& fs, cudaStream_t st);
+                             cudaStream_t st);
 
 // Planes of MQ the FP32 force writes (its K shares; the element-wise step sums them).
 int sgemm_force_planes(int64_t Rp);
@@ -185,12 +173,8 @@ struct TcForce;   // opaque, holds the tensor maps
 cudaError_t tc_force_prepare(TcForce** out, int kind, const void* A_hi, const void* A_lo,
                              const void* B_hi, const void* B_lo, int64_t Np, int64_t Rp,
                              int64_t N, int64_t R, float* MQ);
-// sync (may be NULL): the ForceSync words the row-pair kernel advances.
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
-                         cudaStream_t st, uint32_t* sync = nullptr);
-// For the row-pair kernel: how much one launch advances word 0 (its CTAs) and each row
-// pair's word (its K shares); false (and zeros) for the other force kernels.
-bool tc_force_sync_counts(const TcForce* tf, uint32_t* ctas, uint32_t* kshares);
+                         cudaStream_t st);
 void tc_force_free(TcForce* tf);
 // Test hook: stall_ns > 0 makes later launches issue no copies and end through their
 // timeout path after stall_ns (see fth_test_stall); 0 restores normal launches.

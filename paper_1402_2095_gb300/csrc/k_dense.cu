@@ -28,43 +28,16 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_
                  float* __restrict__ q, float* __restrict__ p, float* __restrict__ s,
                  uint32_t kappa, int flags, int observable, float* __restrict__ ps,
                  int64_t ps_ld, int64_t slot_off, int op_kind, void* op_hi, void* op_lo,
-                 int Np, ForceSync fs) {
+                 int Np) {
     // programmatic dependent launch both ways: this grid may be resident before the force
-    // GEMM it follows has finished.  Without completion counters it waits for that whole
-    // grid; with them, a block waits only until every force CTA has finished reading q^T
-    // (this block overwrites a slice of it) and the force of its own 256-row pair has
-    // landed in MQ.  Then it lets the next force GEMM start its setup on SMs it leaves free
-    // (that kernel waits for this whole grid before reading q).  State loads bypass L1:
-    // without the grid-wide wait, lines an earlier launch left there could be stale.
+    // GEMM it follows has finished, so it waits for it before touching memory; then it
+    // lets the next force GEMM start its setup on SMs it leaves free (that kernel waits
+    // for this grid before reading q)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ float tq[32][33];                 // [replica][row] of the block's tile
-    __shared__ int go;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.x * 32, rp = blockIdx.y * 32;
-    if (fs.words) {
-        if (threadIdx.x == 0) {
-            const uint32_t* rows = fs.words + 1 + (i0 >> 8);
-            uint64_t t0;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-            bool ready = false;
-            for (;;) {
-                uint32_t a, b;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(a) : "l"(fs.words) : "memory");
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(b) : "l"(rows) : "memory");
-                ready = (int32_t)(a - fs.expect_main) >= 0 && (int32_t)(b - fs.expect_rows) >= 0;
-                uint64_t t;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                if (ready || t - t0 > 1000000000ull) break;
-                __nanosleep(128);
-            }
-            if (!ready) atomicOr(fs.err, kErrTimeout);
-            go = ready;
-        }
-        __syncthreads();
-        if (!go) return;                          // uniform over the block
-    } else {
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-    }
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int k = warp * 4 + (lane >> 3);        // row within the tile
     const int i = i0 + k;
     const int c0 = (lane & 7) * 4;               // first replica within the tile
@@ -74,9 +47,9 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_
         const int64_t plane = (int64_t)Np * Rp;
         const int64_t off = (int64_t)i * Rp + r0;
         // the force may arrive as partial sums over K (one plane per K share)
-        float4 mq4 = __ldcg(reinterpret_cast<const float4*>(MQ + off));
+        float4 mq4 = *reinterpret_cast<const float4*>(MQ + off);
         for (int pl = 1; pl < mq_planes; ++pl) {
-            const float4 x = __ldcg(reinterpret_cast<const float4*>(MQ + pl * plane + off));
+            const float4 x = *reinterpret_cast<const float4*>(MQ + pl * plane + off);
             mq4.x += x.x;
             mq4.y += x.y;
             mq4.z += x.z;
@@ -84,11 +57,11 @@ dense_gle_kernel(GleF32 g, int N, int R, int Rp, float* __restrict__ MQ, int mq_
         }
         // the force adds into MQ: leave it zero for the next launch
         if (flags & kZeroMQ) *reinterpret_cast<float4*>(MQ + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 q4 = __ldcg(reinterpret_cast<const float4*>(q + off));
+        float4 q4 = *reinterpret_cast<const float4*>(q + off);
         float4 v4[NS];
-        v4[0] = __ldcg(reinterpret_cast<const float4*>(p + off));
+        v4[0] = *reinterpret_cast<const float4*>(p + off);
 #pragma unroll
-        for (int a = 1; a < NS; ++a) v4[a] = __ldcg(reinterpret_cast<const float4*>(s + (a - 1) * plane + off));
+        for (int a = 1; a < NS; ++a) v4[a] = *reinterpret_cast<const float4*>(s + (a - 1) * plane + off);
 
         const float* qa = reinterpret_cast<const float*>(&q4);
         float samp[4] = {0.f, 0.f, 0.f, 0.f};
@@ -141,7 +114,7 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
                              uint32_t kappa,
                              int flags, int observable, float* ps, int64_t ps_ld, int64_t slot,
                              int op_kind, void* op_hi, void* op_lo, int64_t Np,
-                             const ForceSync& fs, cudaStream_t st) {
+                             cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((N + 31) / 32), (unsigned)((Rp + 31) / 32));
     cfg.blockDim = dim3(256, 1);
@@ -156,8 +129,7 @@ cudaError_t launch_dense_gle(int ns, const GleF32& g, int64_t N, int64_t R, int6
     case NSV: {                                                                               \
         const cudaError_t e = cudaLaunchKernelEx(                                             \
             &cfg, dense_gle_kernel<NSV>, g, (int)N, (int)R, (int)Rp, MQ, mq_planes, q, p, s,  \
-            kappa, flags, observable, ps, ps_ld, slot_off, op_kind, op_hi, op_lo, (int)Np,    \
-            fs);                                                                              \
+            kappa, flags, observable, ps, ps_ld, slot_off, op_kind, op_hi, op_lo, (int)Np);   \
         if (e != cudaSuccess) return e;                                                       \
         break;                                                                                \
     }

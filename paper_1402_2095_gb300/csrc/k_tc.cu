@@ -351,15 +351,11 @@ tc_force_splitk_kernel(const __grid_constant__ TcMaps maps, float* __restrict__ 
 // are added into MQ in L2 by TMA tensor reduce-adds from shared memory (SWIZZLE_128B boxes
 // of 128 rows x 32 columns); MQ is zero at every launch (the element-wise step that reads
 // it writes zeros back).  The order of the KSPLIT additions into an element is not fixed,
-// so MQ can differ in its last bits from run to run.  With `sync` (ForceSync words), each
-// CTA adds 1 to word 0 once its MMAs have completed (its copies of q^T are done) and 1 to
-// word 1 + blockIdx.x once its reduce-adds have landed, on every path, so the element-wise
-// step can start on a row pair before the rest of the grid ends.
+// so MQ can differ in its last bits from run to run.
 template <int STAGES, int KSPLIT>
 __global__ void __launch_bounds__(128, 1)
 tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ CUtensorMap mq,
-                     int Rp, int nslices_total, uint32_t* err, uint64_t stall_ns,
-                     uint32_t* sync) {
+                     int Rp, int nslices_total, uint32_t* err, uint64_t stall_ns) {
     constexpr int kA = 128 * 128;               // one 128-row x 128-B slice of M
     constexpr int kB = 256 * 128;               // 256 replica rows x 128 B of q^T
     constexpr int kStage = 2 * kA + kB;         // 64 KiB
@@ -483,7 +479,6 @@ tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant_
     const bool ok = __syncthreads_and(mbar_wait(done, 0, err) &&
                                       *reinterpret_cast<volatile uint32_t*>(err) == 0);
     fence_after_sync();                         // every stage consumed: reuse them for staging
-    if (sync && threadIdx.x == 0) counter_release_add(sync, 1);   // q^T no longer read
     if (ok && nsl > 0) {
         // four chunks of 128 columns (two per tile), staged alternately in two 64 KiB
         // buffers: a chunk's reduce-adds run while the next chunk is read out of TMEM
@@ -530,11 +525,6 @@ tc_force_pair_kernel(const __grid_constant__ TcMaps maps, const __grid_constant_
             }
         }
         if (threadIdx.x == 0) bulk_wait_all();
-    }
-    if (sync && threadIdx.x == 0) {
-        // this CTA's partial sums are in MQ (or it has none to add)
-        fence_proxy_async_global();
-        counter_release_add(sync + 1 + blockIdx.x, 1);
     }
     fence_before_sync();
     __syncthreads();
@@ -988,8 +978,7 @@ constexpr int kPairStages = 3;
 constexpr int kPairKSplit = 9;
 
 template <int KS>
-static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t st,
-                                  uint32_t* sync) {
+static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t st) {
     const size_t sm = (size_t)kPairStages * (2 * 128 * 128 + 256 * 128) + 1024 +
                       8 * (2 * kPairStages + 2);
     auto kern = tc_force_pair_kernel<kPairStages, KS>;
@@ -1008,36 +997,21 @@ static cudaError_t launch_pair_ks(const TcForce* tf, uint32_t* err, cudaStream_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, tf->maps_wide, tf->mq, (int)tf->Rp, (int)(tf->Np / 32),
-                              err, tf->stall_ns, sync);
+                              err, tf->stall_ns);
 }
 
 // K split 9 fills 144 of the 152 SMs at N = 4096 (16 row pairs x 9; 8 ways left 24 idle);
 // smaller problems split K 18 ways so they still start about as many CTAs (each CTA's
 // partial tile, and so its epilogue, is the same size either way).
-static int pair_ksplit(const TcForce* tf) {
-    return tf->Np / 256 * kPairKSplit >= 96 ? kPairKSplit : 2 * kPairKSplit;
-}
-
-static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st,
-                               uint32_t* sync) {
-    return pair_ksplit(tf) == kPairKSplit ? launch_pair_ks<kPairKSplit>(tf, err, st, sync)
-                                          : launch_pair_ks<2 * kPairKSplit>(tf, err, st, sync);
-}
-
-bool tc_force_sync_counts(const TcForce* tf, uint32_t* ctas, uint32_t* kshares) {
-    if (!tf->pair) {
-        *ctas = *kshares = 0;
-        return false;
-    }
-    *kshares = (uint32_t)pair_ksplit(tf);
-    *ctas = (uint32_t)(tf->Np / 256) * *kshares;
-    return true;
+static cudaError_t launch_pair(const TcForce* tf, uint32_t* err, cudaStream_t st) {
+    return tf->Np / 256 * kPairKSplit >= 96 ? launch_pair_ks<kPairKSplit>(tf, err, st)
+                                            : launch_pair_ks<2 * kPairKSplit>(tf, err, st);
 }
 
 cudaError_t tc_force_run(const TcForce* tf, float* MQ, int64_t ldf, uint32_t* err,
-                         cudaStream_t st, uint32_t* sync) {
+                         cudaStream_t st) {
     if (tf->pair) {
-        const cudaError_t e = launch_pair(tf, err, st, sync);
+        const cudaError_t e = launch_pair(tf, err, st);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (tf->wide) {

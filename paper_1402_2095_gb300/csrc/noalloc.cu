@@ -130,7 +130,7 @@ extern "C" fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t 
     if (cudaGetLastError() != cudaSuccess) return FTH_E_CUDA;
     const int flags = mode == 1 ? kDoStart : (kDoEnd | kDoStart | (sample ? kDoSample : 0));
     if (launch_dense_gle(ns, g, n, replicas, ldr, mq, 1, q, p, s, kappa, flags, FTH_OBS_P, sample,
-                         ldr, 0, kOpNone, nullptr, nullptr, n, ForceSync{}, strm) != cudaSuccess)
+                         ldr, 0, kOpNone, nullptr, nullptr, n, strm) != cudaSuccess)
         return FTH_E_CUDA;
     return FTH_OK;
 }

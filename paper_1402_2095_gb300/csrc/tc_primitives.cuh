@@ -251,18 +251,6 @@ __device__ __forceinline__ void fence_after_sync() {
 }
 
 
-// Release-add on a device-wide counter (orders this thread's earlier memory operations
-// before the increment for any thread that acquires the new value).
-__device__ __forceinline__ void counter_release_add(uint32_t* p, uint32_t v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Writes of completed bulk (async-proxy) operations become ordered with this thread's later
-// generic-proxy operations on global memory.
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // Bring a tensor map (a __grid_constant__ kernel parameter) into the TMA unit's descriptor
 // cache ahead of its first copy, so that fetch overlaps the CTA's setup.
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {

@@ -72,15 +72,16 @@ def test_tensor_core_trajectory(precision, tol):
     assert _trajectory(g, o, 400, 2) <= tol
 
 
-def test_tensor_core_trajectory_row_pair_kernel():
-    """TF32 on whole row pairs (N a multiple of 256, 128 < R <= 256): the row-pair force
-    with L2 reduce-adds, each element-wise block starting once every force CTA has read
-    its q^T and its own row pair's sums have landed (the force's completion counters).
-    400 steps against the oracle on the first 16 of the 256 replicas: replicas evolve
-    independently and draw their own noise, so the oracle needs no others."""
+@pytest.mark.parametrize("n", [512, 470])
+def test_tensor_core_trajectory_row_pair_kernel(n):
+    """TF32 with the padded order a multiple of 256 and 128 < R <= 256: the row-pair force
+    with L2 reduce-adds and the element-wise step that zeroes MQ after reading it, chained
+    by programmatic dependent launch (n = 470 leaves a part-filled row tile and padding
+    rows).  400 steps against the oracle on the first 16 of the 256 replicas: replicas
+    evolve independently and draw their own noise, so the oracle needs no others."""
     from oracle.fth import OracleFTH
     from paper_1402_2095_gb300 import FTH
-    n, R, Ro = 512, 256, 16
+    R, Ro = 256, 16
     a, c = syn.random_gle(4, seed=14, rate=3.0)
     M = _dense(n).astype(np.float32)
     g = FTH(M=M, a_p=a, c_p=c, dt=0.01, replicas=R, seed=5, precision="tf32")
