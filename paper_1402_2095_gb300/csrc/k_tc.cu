@@ -686,6 +686,11 @@ tc_syrk_sq_kernel(const __grid_constant__ TcMaps maps, const __grid_constant__ C
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    // programmatic dependent launch: the setup above overlaps the end of the element-wise
+    // step that filled the stack; nothing of the stack or the partial tiles is touched
+    // before that grid has finished, and the next force may set up during this pass
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int nbw = nbt / 2;
     const int nblk = nbw * (nbw + 1) / 2;
     auto decode = [nbw](int t, int& Iw, int& Jw) {
@@ -1104,9 +1109,23 @@ cudaError_t tc_syrk_run(const TcSyrk* ts, int64_t ncols, float* tiles, uint32_t*
         const size_t sm = (size_t)kSyrkSqStages * 2 * 256 * 128 + kSyrkOutBufs * 128 * 128 +
                           1024 + 8 * (2 * kSyrkSqStages + 4);
         auto kern = tc_syrk_sq_kernel<kSyrkSqStages, kSyrkOutBufs>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<grid, 192, sm, st>>>(ts->maps_wide, ts->part, nbt, nslices, err);
-        return cudaGetLastError();
+        static const bool attr_set =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+            cudaSuccess;
+        (void)attr_set;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid, 1, 1);
+        cfg.blockDim = dim3(192, 1, 1);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e =
+            cudaLaunchKernelEx(&cfg, kern, ts->maps_wide, ts->part, nbt, nslices, err);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (ts->Np >= 256) {
         const int nbw = (nbt + 1) / 2;
