@@ -416,8 +416,9 @@ struct fth_ctx {
     float* ps = nullptr;          // sample stack being filled (one of psb)
     float* psb[2] = {nullptr, nullptr};
     int psi = 0;                  // index of the stack being filled
-    // accumulation passes and block flushes run on a side stream, overlapping the next
-    // steps; events order them against the caller's stream
+    // accumulation passes and block flushes other than the tensor-core pass over all
+    // elements run on a side stream, overlapping the next steps; events order them
+    // against the caller's stream (acc_stream)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     cudaEvent_t ev_join = nullptr;
