@@ -132,7 +132,8 @@ typedef struct {
     size_t workspace_bytes;
 } fth_info_t;
 
-/* Bytes of device workspace fth_create needs for this problem (no device access). */
+/* Bytes of device workspace fth_create needs for this problem (no device access).
+ * Passage: none (device memory of this library; the paper's program ran on CPUs). */
 fth_status fth_workspace_size(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
                               size_t* bytes);
 
@@ -145,7 +146,10 @@ fth_status fth_workspace_size(const fth_matrix* M, const fth_gle* gle, const fth
  * through the part of the workspace that the state will occupy.  A host M is read and
  * not kept.
  * Errors: INVALID_ARG (also non-finite entries), NOT_SPD (a diagonal entry <= 0),
- * UNSUPPORTED, WORKSPACE, CUDA. */
+ * UNSUPPORTED, WORKSPACE, CUDA.
+ * Passage: Eq. 5 (M is the Hessian of the harmonic potential), Eq. 2 and Eq. 4 (the GLE
+ * fixed by A_p and C_p), and the velocity Verlet GLE integrator Sec. "The f-thermostat"
+ * cites. */
 fth_status fth_create(const fth_matrix* M, const fth_gle* gle, const fth_options* opt,
                       void* workspace, size_t workspace_bytes, fth_ctx** out);
 
@@ -155,17 +159,22 @@ fth_status fth_create(const fth_matrix* M, const fth_gle* gle, const fth_options
  * carries per-step values that the context tracks on the host (kick index, stack slot),
  * so the launches of a call are not meant to be
  * captured into a CUDA graph and replayed; fth_dense_step_noalloc is the entry point for
- * capture. */
+ * capture.
+ * Passage: Eq. 2 integrated for every degree of freedom of every replica under the force
+ * of Eq. 5; the samples are the ones Eq. 6 averages. */
 fth_status fth_run(fth_ctx* ctx, int64_t steps);
 
 /* Estimates of <x_i x_j> for k pairs (2k indices): values[e] = mean over every
  * accumulated sample and replica; errbars[e] = standard error of the mean of the
  * completed block means (NaN with fewer than 2 blocks).  Synchronises the stream.
- * Errors: NOT_TRACKED if a pair is not accumulated, NONFINITE, CUDA. */
+ * Errors: NOT_TRACKED if a pair is not accumulated, NONFINITE, CUDA.
+ * Passage: Eq. 6, averaged over time and replicas; the block error bar estimates the
+ * statistical error whose sqrt(tau / t) scaling Sec. "Results and benchmarks" discusses. */
 fth_status fth_elements(fth_ctx* ctx, const int64_t* pairs, int64_t k, double* values,
                         double* errbars);
 
-/* Copy one state plane to / from the host in FP64, layout [R][N] ([R][s][N] for s). */
+/* Copy one state plane to / from the host in FP64, layout [R][N] ([R][s][N] for s).
+ * Passage: none (state access for checks and restarts). */
 fth_status fth_get_state(fth_ctx* ctx, int plane, double* host);
 
 /* Linear functionals of tracked elements, L = sum_k w_k <x_{i_k} x_{j_k}>: the trace
@@ -222,6 +231,8 @@ fth_status fth_untransform_trace(int kind, const double* params, int64_t n, doub
                                  double* errbar);
 fth_status fth_set_state(fth_ctx* ctx, int plane, const double* host);
 
+/* Context housekeeping (info, error word, messages, release).  Passage: none. */
+
 /* Counters and configuration of a context. */
 fth_status fth_info(const fth_ctx* ctx, fth_info_t* info);
 
@@ -235,7 +246,9 @@ const char* fth_last_error(const fth_ctx* ctx);
 void fth_destroy(fth_ctx* ctx);
 
 /* The library's own O half-step constants in FP64: T = exp(-A_p dt/2) (Pade scaling
- * and squaring) and lower-triangular S with S S^T = C_p - T C_p T^T; (s+1)^2 each. */
+ * and squaring) and lower-triangular S with S S^T = C_p - T C_p T^T; (s+1)^2 each.
+ * Passage: the thermostat part of Eq. 2 for A_p and C_p (Eq. 4), as the exact
+ * Ornstein-Uhlenbeck half-step of the integrator Sec. "The f-thermostat" cites. */
 fth_status fth_gle_propagator(const fth_gle* gle, double dt, double* T, double* S);
 
 /* ----------------------------------------------------------------------------------
@@ -329,7 +342,8 @@ enum fth_kernel_class {
 };
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel the context launches:
- * one event pair around each launch on the context's stream (off by default). */
+ * one event pair around each launch on the context's stream (off by default).
+ * Passage: none (measurement), as for fth_profile_read and fth_test_stall. */
 fth_status fth_profile_enable(fth_ctx* ctx, int enable);
 
 /* Synchronise, then return per kernel class the summed device milliseconds and the
@@ -377,6 +391,8 @@ fth_status fth_dense_step_noalloc(const float* M, int64_t n, int64_t ldm, float*
                                   uint32_t kappa, int mode, float* sample, void* stream);
 
 /* ----------------------------------------------------------------------------------
+ * Passage: Sec. "Final discussion" (independent simulations that run side by side); the
+ * arithmetic per problem is that of fth_create / fth_run.
  * Problem pools: many independent problems resident on one device and stepped together
  * (ragged batches, continuous batching).  Problems of different order and kind (dense
  * or CSR) share one set of launches per step: a persistent tensor-core force kernel
@@ -477,6 +493,8 @@ const char* fth_pool_last_error(const fth_pool* pool);
 void fth_pool_destroy(fth_pool* pool);
 
 /* ----------------------------------------------------------------------------------
+ * Passage: none beyond the pool's (a scheduling policy over independent problems; the
+ * retirement rule is the block error bar of fth_elements).
  * Serving loop over a pool: requests are queued on submit, admitted into the pool when
  * a slot and enough workspace are free (arrival order; a request that does not fit is
  * passed by later ones at most max_bypass times), stepped together with all others
